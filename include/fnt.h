@@ -1,0 +1,279 @@
+/*
+ * fnt.h -- C ABI of libfnt: Fermat-number-transform chromatic dispersion
+ * compensation (FNT-CDC) and adaptive equalisation (FNT-AEQ) on one GB300 GPU.
+ *
+ * Method: S. Chen et al., "Fermat Number Transform Based Chromatic Dispersion
+ * Compensation and Adaptive Equalization Algorithm", arXiv 2405.04253.
+ *   eq. (1)/(2)  length-N transform pair over Z_F, F = 2^16 + 1
+ *   eq. (3)/(4)  conditions on F and the radix alpha
+ *   eq. (5)      overflow constraint that makes the integer result exact
+ *   eq. (6)      RDE tap update of the 4x4 real-valued MIMO equaliser
+ *   eq. (7)/(8)  complex convolution from two real products
+ *   CDC: F = 65537, alpha = sqrt(2) (= 4080), N = 64, 5-bit signal, 6-bit taps
+ *   AEQ: F = 65537, alpha = 2, N = 32, 5-bit signal, 14-bit taps in two 7-bit groups
+ *
+ * Conventions for every call:
+ *   - Nothing throws.  Every call returns an fnt_status; fnt_last_error() gives
+ *     the detail text of the last failure on the calling thread.
+ *   - Sample buffers are int8 / int16 arrays owned by the caller.  Unless a call
+ *     says otherwise they are DEVICE pointers on the current CUDA device.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that take a stream only enqueue work on it and return; results are
+ *     ready when the stream reaches that point.
+ *   - Host arrays passed in (frame tables, taps, tap state) are read before the
+ *     call returns and may be reused right after.
+ *   - All results are bit-exact integers: the same on every run and every launch
+ *     shape.
+ */
+#ifndef FNT_H
+#define FNT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FNT_API __attribute__((visibility("default")))
+#else
+#define FNT_API
+#endif
+
+typedef enum fnt_status {
+    FNT_OK = 0,
+    FNT_ERR_INVALID = 1,   /* bad argument, shape or pointer */
+    FNT_ERR_BOUND = 2,     /* parameters violate eq. (4) or constraint (5) */
+    FNT_ERR_NOMEM = 3,     /* device or host allocation failed */
+    FNT_ERR_BUSY = 4,      /* session admission refused: memory cap or slots full */
+    FNT_ERR_TIMEOUT = 5,   /* poll timed out with nothing completed */
+    FNT_ERR_CUDA = 6,      /* a CUDA runtime call failed (detail in fnt_last_error) */
+    FNT_ERR_NOT_FOUND = 7  /* unknown link or ticket */
+} fnt_status;
+
+/* Copies the calling thread's last error text into buf (always NUL-terminated).
+ * Returns the full length of the message. */
+FNT_API size_t fnt_last_error(char *buf, size_t len);
+
+/* Library version, e.g. "fnt 1.0 sm_103a". */
+FNT_API const char *fnt_version(void);
+
+/* ------------------------------------------------------------------ plan ---- */
+
+/*
+ * Parameters of one CDC -> resample -> AEQ configuration.
+ *
+ * n_cdc, alpha_cdc   CDC transform length and radix.  Supported: 64 with 4080
+ *                    (sqrt 2 mod 65537, section "Proposed FNT-CDC&AEQ structure").
+ * cdc_step           overlap-save step S (new samples per 64-sample block).
+ *                    0 = N - L + 1 for each frame's tap count L.  Must satisfy
+ *                    32 <= S <= N - L + 1 for every frame (the zero padding that
+ *                    turns circular into linear convolution, text after eq. (5)).
+ * n_aeq, alpha_aeq   AEQ transform length and radix: 32 with 2 (the paper's AEQ)
+ *                    or 64 with 4080.
+ * aeq_taps           K, taps per real filter of the 4x4 MIMO: must be 16.
+ *                    The AEQ step is n_aeq - K symbols per block.
+ * mu_shift           m: the update of eq. (6) is applied as floor(G / 2^m);
+ *                    0 <= m <= 62, or 63 for mu = 0 (taps held fixed).
+ * rde_a              A: the 16QAM ring radii of the RDE error are sqrt(2, 10, 18) A,
+ *                    1 <= A <= 4096.
+ * tap_init           w0: initial taps are w0 (Q1.13) at centre tap K/2 of the four
+ *                    diagonal filters XI->XI, XQ->XQ, YI->YI, YQ->YQ, 0 elsewhere.
+ * aeq_segment        symbols per AEQ segment for long streams; 0 = one serial run
+ *                    per frame.  With segments, output segment s covers symbols
+ *                    [s*seg, (s+1)*seg) and its AEQ run starts aeq_warmup symbols
+ *                    earlier (not before 0) from the plan's initial taps with zero
+ *                    history, as if that slice were a frame of its own; only the
+ *                    segment's own outputs are kept.  Segments run in parallel.
+ * aeq_warmup         warm-up symbols of each segment (ignored without segments).
+ */
+typedef struct fnt_plan_desc {
+    int32_t n_cdc;
+    int32_t alpha_cdc;
+    int32_t cdc_step;
+    int32_t n_aeq;
+    int32_t alpha_aeq;
+    int32_t aeq_taps;
+    int32_t mu_shift;
+    int32_t rde_a;
+    int32_t tap_init;
+    int32_t reserved;
+    int64_t aeq_segment;
+    int64_t aeq_warmup;
+} fnt_plan_desc;
+
+/* Fills *desc with the defaults: N=64/4080, S = N-L+1, AEQ N=32/2, K=16, m=10,
+ * A=64, w0=2048, no segments. */
+FNT_API void fnt_plan_desc_default(fnt_plan_desc *desc);
+
+typedef struct fnt_plan fnt_plan;
+
+/* Validates desc (eq. (4): alpha^N = 1 with order exactly N, N invertible mod F;
+ * supported (N, alpha) pairs; ranges above) and creates a plan.  A plan holds no
+ * per-call state and may be used from several threads and streams at once.
+ * Errors: FNT_ERR_INVALID, FNT_ERR_BOUND, FNT_ERR_NOMEM. */
+FNT_API fnt_status fnt_plan_create(const fnt_plan_desc *desc, fnt_plan **out);
+FNT_API fnt_status fnt_plan_destroy(fnt_plan *plan);
+
+/* ---------------------------------------------------------------- frames ---- */
+
+/*
+ * One independent frame.
+ *   in        samples.  CDC and chain: int8 [n][n_pol][2] (I, Q), 5-bit signed
+ *             [-16, 15], 2 samples per symbol.  AEQ alone: int8 [n][4]
+ *             (XI, XQ, YI, YQ), 5-bit signed, 1 sample per symbol.
+ *   out       results.  CDC: int16 [n][n_pol][2], the exact complex convolution
+ *             z[t] = sum_k h[k] x[t-k] (zero history, no delay compensation).
+ *             Chain: int16 [n_sym][4] AEQ output at 1 sample per symbol with
+ *             n_sym = ceil((n - phase) / 2), phase = ((L - 1) / 2) mod 2.
+ *             AEQ alone: int16 [n][4].
+ *   cd_taps   HOST int8 [cd_len][2] (re, im), 6-bit signed [-32, 31]; CDC and
+ *             chain only (ignored by the AEQ alone).
+ *   aeq_state DEVICE int32 [4 (S2)][4 (S1)][K] master taps of the AEQ
+ *             (tap = state >> 16), read at the start and overwritten with the
+ *             adapted taps at the end; NULL = start from the plan's initial taps
+ *             and keep nothing.  With AEQ segments every segment starts from the
+ *             plan's initial taps and the state, if given, only receives the
+ *             final taps of the last segment.  Ignored by the CDC.
+ *   n         samples (CDC, chain) or symbols (AEQ alone); 0 is allowed.
+ *   n_pol     1 or 2 for the CDC; 2 for the chain; ignored by the AEQ alone.
+ *   cd_len    L, 1..31 (31 * 2 * 16 * 32 = 31744 keeps every output inside int16
+ *             and inside constraint (5)); with n_pol = 2 both polarisations use
+ *             the same taps.
+ */
+typedef struct fnt_frame {
+    const void *in;
+    void *out;
+    const int8_t *cd_taps;
+    int32_t *aeq_state;
+    int64_t n;
+    int32_t n_pol;
+    int32_t cd_len;
+} fnt_frame;
+
+/*
+ * A batch of frames processed by one call.  `frames` is a HOST array.
+ * host_buffers = 0: in/out of every frame are device pointers.
+ * host_buffers = 1: in/out are host pointers (page-locked or pageable); the
+ *                   library copies inputs in and outputs back through device
+ *                   memory of its own, and the call returns only after the
+ *                   outputs are in host memory.
+ */
+typedef struct fnt_frame_batch {
+    int32_t n_frames;
+    int32_t host_buffers;
+    const fnt_frame *frames;
+} fnt_frame_batch;
+
+/* FNT-CDC alone (sections "Fermat number transform" and "Proposed FNT-CDC&AEQ
+ * structure": eqs. (1), (2), (5), (7), (8)).  Errors: FNT_ERR_INVALID (shapes,
+ * tap values outside 6 bits), FNT_ERR_BOUND (cd_len or step beyond eq. (5) /
+ * the zero padding), FNT_ERR_NOMEM, FNT_ERR_CUDA. */
+FNT_API fnt_status fnt_cdc_run(const fnt_plan *plan, const fnt_frame_batch *batch, void *stream);
+
+/* FNT-AEQ alone on 1-sample/symbol 5-bit PDM input (eq. (6) and the 4x4
+ * RV-MIMO with two 7-bit tap groups).  Each frame is one serial run, or
+ * segmented when the plan says so.  Errors as fnt_cdc_run. */
+FNT_API fnt_status fnt_aeq_run(const fnt_plan *plan, const fnt_frame_batch *batch, void *stream);
+
+/* The receiver chain of the experimental section: FNT-CDC on both
+ * polarisations, requantisation of the CDC output to 5 bits
+ * (x = sat[-16,15](floor((z + 2^(s-1)) / 2^s)), s = floor(bitlen(E) / 2),
+ * E = sum_k |h[k]|^2), resampling to 1 sample/symbol (times t = phase mod 2),
+ * then FNT-AEQ.  Errors as fnt_cdc_run. */
+FNT_API fnt_status fnt_cdc_aeq_run(const fnt_plan *plan, const fnt_frame_batch *batch, void *stream);
+
+/* ------------------------------------------------------ prepared batches ---- */
+
+typedef enum fnt_op { FNT_OP_CDC = 0, FNT_OP_AEQ = 1, FNT_OP_CHAIN = 2 } fnt_op;
+
+typedef struct fnt_batch fnt_batch;
+
+/*
+ * Prepares a batch once for repeated launches: validates it, builds the work
+ * lists (frames split into 32-block CDC items; AEQ chains or segments sorted
+ * longest first), uploads them and allocates the intermediate buffers, all in
+ * device memory owned by the fnt_batch.  Device pointers only (host_buffers must
+ * be 0).  use_graph = 1 records the launch into a CUDA graph on the first
+ * fnt_batch_launch and replays it afterwards.
+ */
+FNT_API fnt_status fnt_batch_create(const fnt_plan *plan, const fnt_frame_batch *batch, int32_t op,
+                            int32_t use_graph, fnt_batch **out);
+
+/* Enqueues the prepared work on `stream`.  Launches of one fnt_batch must not
+ * overlap on the device (they share its intermediate buffers). */
+FNT_API fnt_status fnt_batch_launch(fnt_batch *b, void *stream);
+
+/* Number of kernel launches one fnt_batch_launch enqueues. */
+FNT_API int32_t fnt_batch_kernel_count(const fnt_batch *b);
+
+FNT_API fnt_status fnt_batch_destroy(fnt_batch *b);
+
+/* Sets the warps per CTA and, for the AEQ, CTAs per SM used by later
+ * launches of this plan (autotuner hook).  0 keeps the current value. */
+FNT_API fnt_status fnt_plan_set_launch(fnt_plan *plan, int32_t cdc_warps, int32_t aeq_warps);
+
+/* ---------------------------------------------------------------- serving ---- */
+
+/*
+ * Continuous-batching session over n_links links.  Each link has fixed CD taps
+ * and an AEQ tap state that stays in device memory and carries from one of the
+ * link's frames to the next (frames of a link run in submission order; the
+ * delay line does not carry).  Requests are admitted while the session's device
+ * memory (inputs, outputs, intermediate buffers and work lists of admitted
+ * requests) stays within mem_cap_bytes; the scheduler packs ready frames of
+ * idle links into waves and runs up to n_streams waves at once, so requests
+ * admitted while others run overlap with them on the device.
+ */
+typedef struct fnt_session fnt_session;
+
+typedef struct fnt_completion {
+    uint64_t ticket;
+    int32_t link;
+    int32_t status;          /* fnt_status of this request */
+    int64_t n_sym;           /* symbols written */
+    double submit_us;        /* host steady-clock times, microseconds */
+    double start_us;         /* its wave was launched */
+    double done_us;          /* completion was observed */
+} fnt_completion;
+
+FNT_API fnt_status fnt_session_create(const fnt_plan *plan, int32_t n_links, size_t mem_cap_bytes,
+                              int32_t n_streams, fnt_session **out);
+
+/* Fixed CD taps of a link (HOST int8 [L][2]); resets its AEQ state to the plan's
+ * initial taps.  Not allowed while the link has requests in the session. */
+FNT_API fnt_status fnt_session_set_link(fnt_session *s, int32_t link, const int8_t *cd_taps, int32_t L);
+
+/* Submits one PDM frame: in = int8 [n][2][2], out = int16 [n_sym][4] (as for
+ * fnt_cdc_aeq_run).  Both are either device pointers or page-locked host
+ * pointers (the session copies through its own device memory); pageable host
+ * memory is rejected with FNT_ERR_INVALID.  The buffers must stay valid until
+ * the request completes.  Returns FNT_ERR_BUSY, admitting nothing, when the
+ * request does not fit under the memory cap right now. */
+FNT_API fnt_status fnt_session_submit(fnt_session *s, int32_t link, const void *in, int64_t n, void *out,
+                              uint64_t *ticket);
+
+/* Drives the scheduler and collects finished requests (at most max_done).  Waits
+ * up to timeout_us for at least one completion (0 = do not wait); returns
+ * FNT_ERR_TIMEOUT when nothing completed in that time. */
+FNT_API fnt_status fnt_session_poll(fnt_session *s, int32_t timeout_us, fnt_completion *done,
+                            int32_t max_done, int32_t *n_done);
+
+/* Requests admitted and not yet returned by fnt_session_poll. */
+FNT_API int32_t fnt_session_pending(const fnt_session *s);
+
+/* Checkpoint / resume of a link's AEQ state (HOST int32 [4][4][K]).  The link
+ * must have no request in the session.  Resuming with a saved state gives the
+ * same results, bit for bit, as never having stopped. */
+FNT_API fnt_status fnt_session_get_link_state(fnt_session *s, int32_t link, int32_t *state);
+FNT_API fnt_status fnt_session_set_link_state(fnt_session *s, int32_t link, const int32_t *state);
+
+/* Waits for every admitted request, then frees the session. */
+FNT_API fnt_status fnt_session_destroy(fnt_session *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FNT_H */

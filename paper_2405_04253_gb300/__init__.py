@@ -1,0 +1,227 @@
+"""GB300 (sm_103a) FNT-CDC / FNT-AEQ: Python binding of libfnt.
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+libfnt.so (built in-tree by :func:`build`).  PyTorch supplies device memory and
+streams; tensors are passed to the C ABI (include/fnt.h) as raw pointers.
+There is no CPU fallback: without the library or a GPU every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB, build  # noqa: F401
+
+FNT_OK, FNT_ERR_INVALID, FNT_ERR_BOUND, FNT_ERR_NOMEM, FNT_ERR_BUSY, FNT_ERR_TIMEOUT, FNT_ERR_CUDA, \
+    FNT_ERR_NOT_FOUND = range(8)
+OP_CDC, OP_AEQ, OP_CHAIN = 0, 1, 2
+
+_STATUS = {0: "FNT_OK", 1: "FNT_ERR_INVALID", 2: "FNT_ERR_BOUND", 3: "FNT_ERR_NOMEM", 4: "FNT_ERR_BUSY",
+           5: "FNT_ERR_TIMEOUT", 6: "FNT_ERR_CUDA", 7: "FNT_ERR_NOT_FOUND"}
+
+
+class FntError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("n_cdc", ctypes.c_int32), ("alpha_cdc", ctypes.c_int32), ("cdc_step", ctypes.c_int32),
+                ("n_aeq", ctypes.c_int32), ("alpha_aeq", ctypes.c_int32), ("aeq_taps", ctypes.c_int32),
+                ("mu_shift", ctypes.c_int32), ("rde_a", ctypes.c_int32), ("tap_init", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("aeq_segment", ctypes.c_int64), ("aeq_warmup", ctypes.c_int64)]
+
+
+class FrameC(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("cd_taps", ctypes.c_void_p),
+                ("aeq_state", ctypes.c_void_p), ("n", ctypes.c_int64), ("n_pol", ctypes.c_int32),
+                ("cd_len", ctypes.c_int32)]
+
+
+class BatchC(ctypes.Structure):
+    _fields_ = [("n_frames", ctypes.c_int32), ("host_buffers", ctypes.c_int32),
+                ("frames", ctypes.POINTER(FrameC))]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("link", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("n_sym", ctypes.c_int64), ("submit_us", ctypes.c_double), ("start_us", ctypes.c_double),
+                ("done_us", ctypes.c_double)]
+
+
+# Every symbol include/fnt.h declares, with (restype, argtypes).
+_VP, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+SIGNATURES = {
+    "fnt_last_error": (_SZ, [ctypes.c_char_p, _SZ]),
+    "fnt_version": (ctypes.c_char_p, []),
+    "fnt_plan_desc_default": (None, [ctypes.POINTER(PlanDesc)]),
+    "fnt_plan_create": (_I32, [ctypes.POINTER(PlanDesc), ctypes.POINTER(_VP)]),
+    "fnt_plan_destroy": (_I32, [_VP]),
+    "fnt_plan_set_launch": (_I32, [_VP, _I32, _I32]),
+    "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
+    "fnt_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
+    "fnt_cdc_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
+    "fnt_batch_create": (_I32, [_VP, ctypes.POINTER(BatchC), _I32, _I32, ctypes.POINTER(_VP)]),
+    "fnt_batch_launch": (_I32, [_VP, _VP]),
+    "fnt_batch_kernel_count": (_I32, [_VP]),
+    "fnt_batch_destroy": (_I32, [_VP]),
+    "fnt_session_create": (_I32, [_VP, _I32, _SZ, _I32, ctypes.POINTER(_VP)]),
+    "fnt_session_set_link": (_I32, [_VP, _I32, _VP, _I32]),
+    "fnt_session_submit": (_I32, [_VP, _I32, _VP, _I64, _VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "fnt_session_poll": (_I32, [_VP, _I32, ctypes.POINTER(Completion), _I32, ctypes.POINTER(_I32)]),
+    "fnt_session_pending": (_I32, [_VP]),
+    "fnt_session_get_link_state": (_I32, [_VP, _I32, _VP]),
+    "fnt_session_set_link_state": (_I32, [_VP, _I32, _VP]),
+    "fnt_session_destroy": (_I32, [_VP]),
+}
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Loads libfnt.so (building it first if needed).  Raises if it cannot."""
+    global _lib
+    if _lib is None:
+        p = path or os.environ.get("FNT_LIB") or build()
+        L = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            if hasattr(L, name):
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    lib().fnt_last_error(buf, 1024)
+    return buf.value.decode()
+
+
+def check(status: int) -> None:
+    if status != FNT_OK:
+        raise FntError(status, last_error())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def default_desc(**over) -> PlanDesc:
+    d = PlanDesc()
+    lib().fnt_plan_desc_default(ctypes.byref(d))
+    for k, v in over.items():
+        setattr(d, k, v)
+    return d
+
+
+class Plan:
+    """A validated CDC / AEQ configuration (fnt_plan)."""
+
+    def __init__(self, **over):
+        self.desc = default_desc(**over)
+        h = ctypes.c_void_p()
+        check(lib().fnt_plan_create(ctypes.byref(self.desc), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().fnt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_launch(self, cdc_warps: int = 0, aeq_warps: int = 0):
+        check(lib().fnt_plan_set_launch(self.handle, cdc_warps, aeq_warps))
+
+
+class Frame:
+    """One frame: `x` input, `out` result, `taps` int8 [L, 2] numpy (host),
+    `state` int32 [4, 4, 16] device tensor or None.  `n` is the sample (or,
+    for the AEQ alone, symbol) count; it defaults to x.shape[0]."""
+
+    def __init__(self, x, out, taps=None, state=None, n: int | None = None, n_pol: int = 2):
+        self.x, self.out, self.state = x, out, state
+        self.taps = None if taps is None else np.ascontiguousarray(taps, dtype=np.int8)
+        self.n = int(x.shape[0]) if n is None else int(n)
+        self.n_pol = n_pol
+
+    def c(self) -> FrameC:
+        return FrameC(_ptr(self.x), _ptr(self.out), _ptr(self.taps), _ptr(self.state), self.n, self.n_pol,
+                      0 if self.taps is None else self.taps.shape[0])
+
+
+def _batch(frames, host: bool):
+    arr = (FrameC * max(1, len(frames)))(*[f.c() for f in frames])
+    return BatchC(len(frames), 1 if host else 0, arr), arr
+
+
+def cdc_run(plan: Plan, frames, stream=None, host: bool = False):
+    b, keep = _batch(frames, host)
+    check(lib().fnt_cdc_run(plan.handle, ctypes.byref(b), None if host and stream is None else _stream_handle(stream)))
+
+
+def aeq_run(plan: Plan, frames, stream=None, host: bool = False):
+    b, keep = _batch(frames, host)
+    check(lib().fnt_aeq_run(plan.handle, ctypes.byref(b), None if host and stream is None else _stream_handle(stream)))
+
+
+def cdc_aeq_run(plan: Plan, frames, stream=None, host: bool = False):
+    b, keep = _batch(frames, host)
+    check(lib().fnt_cdc_aeq_run(plan.handle, ctypes.byref(b),
+                                None if host and stream is None else _stream_handle(stream)))
+
+
+class Batch:
+    """A prepared batch (fnt_batch): work lists built and uploaded once."""
+
+    def __init__(self, plan: Plan, frames, op: int, use_graph: bool = True):
+        self.plan, self.frames = plan, frames
+        b, keep = _batch(frames, False)
+        h = ctypes.c_void_p()
+        check(lib().fnt_batch_create(plan.handle, ctypes.byref(b), op, 1 if use_graph else 0, ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        check(lib().fnt_batch_launch(self.handle, _stream_handle(stream)))
+
+    def kernel_count(self) -> int:
+        return int(lib().fnt_batch_kernel_count(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().fnt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def chain_nsym(n: int, L: int) -> int:
+    """Symbols the chain writes for n samples and L CD taps."""
+    phase = ((L - 1) // 2) & 1
+    return max(0, (n - phase + 1) // 2)

@@ -1,0 +1,531 @@
+// api.cu -- host side of libfnt: plans, frame validation, work lists, batch
+// execution and the C ABI entry points declared in include/fnt.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fnt.h"
+#include "host.h"
+#include "internal.h"
+
+namespace fnt {
+
+// ------------------------------------------------------------------ errors ---
+
+static thread_local std::string t_err;
+
+fnt_status fail(fnt_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return st;
+}
+
+fnt_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(FNT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ field checks ---
+
+static constexpr int64_t kF = 65537;   // F_4 = 2^16 + 1
+
+static int64_t hmod(int64_t v) { return ((v % kF) + kF) % kF; }
+
+static int64_t hpow(int64_t a, int64_t e) {
+    int64_t r = 1, b = hmod(a);
+    while (e > 0) {
+        if (e & 1) r = r * b % kF;
+        b = b * b % kF;
+        e >>= 1;
+    }
+    return r;
+}
+
+// eq. (4) for the prime F = 65537, plus order exactly N and N invertible.
+static bool valid_transform(int64_t N, int64_t alpha) {
+    if (N < 2 || hmod(alpha) == 0) return false;
+    if (hpow(alpha, N) != 1) return false;
+    for (int64_t d = 1; d < N; ++d)
+        if (N % d == 0 && hpow(alpha, d) == 1) return false;
+    return hmod(N) != 0;
+}
+
+int cdc_shift_of(const int8_t *taps, int L) {
+    int64_t E = 0;
+    for (int k = 0; k < L; ++k) E += (int64_t)taps[2 * k] * taps[2 * k] + (int64_t)taps[2 * k + 1] * taps[2 * k + 1];
+    int bl = 0;
+    while (E > 0) {
+        ++bl;
+        E >>= 1;
+    }
+    return bl / 2;
+}
+
+int decim_phase_of(int L) { return ((L - 1) / 2) & 1; }
+
+int64_t chain_nsym(int64_t n, int phase) { return n > phase ? (n - phase + 1) / 2 : 0; }
+
+}  // namespace fnt
+
+using namespace fnt;
+
+// --------------------------------------------------------------------- ABI ---
+
+extern "C" size_t fnt_last_error(char *buf, size_t len) {
+    if (buf && len) {
+        size_t m = std::min(len - 1, t_err.size());
+        memcpy(buf, t_err.data(), m);
+        buf[m] = 0;
+    }
+    return t_err.size();
+}
+
+extern "C" const char *fnt_version(void) { return "fnt 1.0 sm_103a"; }
+
+extern "C" void fnt_plan_desc_default(fnt_plan_desc *d) {
+    if (!d) return;
+    memset(d, 0, sizeof *d);
+    d->n_cdc = 64;
+    d->alpha_cdc = 4080;
+    d->cdc_step = 0;
+    d->n_aeq = 32;
+    d->alpha_aeq = 2;
+    d->aeq_taps = 16;
+    d->mu_shift = 10;
+    d->rde_a = 64;
+    d->tap_init = 2048;
+    d->aeq_segment = 0;
+    d->aeq_warmup = 0;
+}
+
+static bool g_configured = false;
+
+static fnt_status configure_kernels() {
+    if (g_configured) return FNT_OK;
+    cudaError_t e = cdc_configure();
+    if (e != cudaSuccess) return cuda_fail(e, "cdc_configure");
+    e = aeq_configure();
+    if (e != cudaSuccess) return cuda_fail(e, "aeq_configure");
+    g_configured = true;
+    return FNT_OK;
+}
+
+extern "C" fnt_status fnt_plan_create(const fnt_plan_desc *d, fnt_plan **out) {
+    if (!d || !out) return fail(FNT_ERR_INVALID, "plan_create: null argument");
+    *out = nullptr;
+    if (!valid_transform(d->n_cdc, d->alpha_cdc))
+        return fail(FNT_ERR_BOUND, "CDC: alpha=%d is not of order N=%d mod 65537 (eq. (4))", d->alpha_cdc, d->n_cdc);
+    if (!valid_transform(d->n_aeq, d->alpha_aeq))
+        return fail(FNT_ERR_BOUND, "AEQ: alpha=%d is not of order N=%d mod 65537 (eq. (4))", d->alpha_aeq, d->n_aeq);
+    if (d->n_cdc != 64 || d->alpha_cdc != 4080)
+        return fail(FNT_ERR_INVALID, "CDC: only N=64 with alpha=4080 is compiled");
+    if (!((d->n_aeq == 32 && d->alpha_aeq == 2) || (d->n_aeq == 64 && d->alpha_aeq == 4080)))
+        return fail(FNT_ERR_INVALID, "AEQ: only (N=32, alpha=2) and (N=64, alpha=4080) are compiled");
+    if (d->aeq_taps != kAeqK) return fail(FNT_ERR_INVALID, "AEQ: aeq_taps must be %d", kAeqK);
+    if (d->cdc_step != 0 && (d->cdc_step < 32 || d->cdc_step > 64))
+        return fail(FNT_ERR_INVALID, "CDC: cdc_step must be 0 or in [32, 64]");
+    if (d->mu_shift < 0 || d->mu_shift > 63) return fail(FNT_ERR_INVALID, "mu_shift must be in [0, 63]");
+    if (d->rde_a < 1 || d->rde_a > 4096) return fail(FNT_ERR_INVALID, "rde_a must be in [1, 4096]");
+    if (d->tap_init < -8192 || d->tap_init > 8191) return fail(FNT_ERR_INVALID, "tap_init must be a 14-bit tap");
+    if (d->aeq_segment < 0 || d->aeq_warmup < 0) return fail(FNT_ERR_INVALID, "negative AEQ segment/warmup");
+    fnt_status st = configure_kernels();
+    if (st != FNT_OK) return st;
+
+    fnt_plan *p = new (std::nothrow) fnt_plan();
+    if (!p) return fail(FNT_ERR_NOMEM, "plan_create: out of host memory");
+    p->d = *d;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device);
+    int32_t init[16 * kAeqK] = {0};
+    for (int s = 0; s < 4; ++s) init[(s * 4 + s) * kAeqK + kAeqK / 2] = (int32_t)((int64_t)d->tap_init * 65536);
+    memcpy(p->h_init, init, sizeof init);
+    e = cudaMalloc(&p->d_init, sizeof init);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaMalloc(init taps)");
+    }
+    e = cudaMemcpy(p->d_init, init, sizeof init, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->d_init);
+        delete p;
+        return cuda_fail(e, "cudaMemcpy(init taps)");
+    }
+    *out = p;
+    return FNT_OK;
+}
+
+extern "C" fnt_status fnt_plan_destroy(fnt_plan *p) {
+    if (!p) return FNT_OK;
+    cudaFree(p->d_init);
+    delete p;
+    return FNT_OK;
+}
+
+extern "C" fnt_status fnt_plan_set_launch(fnt_plan *p, int32_t cdc_warps, int32_t aeq_warps) {
+    if (!p) return fail(FNT_ERR_INVALID, "null plan");
+    if (cdc_warps < 0 || cdc_warps > 4 || aeq_warps < 0 || aeq_warps > 4)
+        return fail(FNT_ERR_INVALID, "warps per CTA must be in [1, 4]");
+    if (cdc_warps) p->cdc_warps = cdc_warps;
+    if (aeq_warps) p->aeq_warps = aeq_warps;
+    return FNT_OK;
+}
+
+// ---------------------------------------------------------- work building ---
+
+namespace fnt {
+
+static bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+// Validates one frame for `op` and fills its DevFrame (pointers as given).
+static fnt_status make_frame(const fnt_plan *p, const fnt_frame &f, int op, int idx, DevFrame &df) {
+    memset(&df, 0, sizeof df);
+    if (f.n < 0) return fail(FNT_ERR_INVALID, "frame %d: n < 0", idx);
+    df.in = (const int8_t *)f.in;
+    df.out = f.out;
+    df.state = f.aeq_state;
+    df.n = f.n;
+    if (op == FNT_OP_AEQ) {
+        df.n_pol = 2;
+        df.n_sym = f.n;
+        df.aeq_in = (int8_t *)f.in;
+        if (f.n > 0 && (!f.in || !f.out)) return fail(FNT_ERR_INVALID, "frame %d: null buffer", idx);
+        if (!aligned(f.in, 4) || !aligned(f.out, 4) || !aligned(f.aeq_state, 4))
+            return fail(FNT_ERR_INVALID, "frame %d: buffers must be 4-byte aligned", idx);
+        return FNT_OK;
+    }
+    if (f.n_pol != 1 && f.n_pol != 2) return fail(FNT_ERR_INVALID, "frame %d: n_pol must be 1 or 2", idx);
+    if (op == FNT_OP_CHAIN && f.n_pol != 2) return fail(FNT_ERR_INVALID, "frame %d: the chain needs n_pol = 2", idx);
+    if (f.cd_len < 1) return fail(FNT_ERR_INVALID, "frame %d: cd_len < 1", idx);
+    if (f.cd_len > kMaxCdTaps)
+        return fail(FNT_ERR_BOUND, "frame %d: cd_len %d > %d breaks constraint (5) for 5-bit x 6-bit with int16 output",
+                    idx, f.cd_len, kMaxCdTaps);
+    if (!f.cd_taps) return fail(FNT_ERR_INVALID, "frame %d: null cd_taps", idx);
+    for (int k = 0; k < 2 * f.cd_len; ++k) {
+        if (f.cd_taps[k] < -32 || f.cd_taps[k] > 31)
+            return fail(FNT_ERR_INVALID, "frame %d: tap value %d outside 6 bits", idx, f.cd_taps[k]);
+        df.taps[k] = f.cd_taps[k];
+    }
+    const int S = p->d.cdc_step ? p->d.cdc_step : kCdcN - f.cd_len + 1;
+    if (S > kCdcN - f.cd_len + 1 || S < 32)
+        return fail(FNT_ERR_BOUND, "frame %d: step %d with %d taps: need 32 <= S <= N - L + 1", idx, S, f.cd_len);
+    df.n_pol = f.n_pol;
+    df.L = f.cd_len;
+    df.S = S;
+    df.shift = cdc_shift_of(f.cd_taps, f.cd_len);
+    df.phase = decim_phase_of(f.cd_len);
+    if (f.n > 0 && (!f.in || !f.out)) return fail(FNT_ERR_INVALID, "frame %d: null buffer", idx);
+    if (!aligned(f.in, 2 * f.n_pol)) return fail(FNT_ERR_INVALID, "frame %d: input must be %d-byte aligned", idx, 2 * f.n_pol);
+    if (op == FNT_OP_CDC) {
+        if (!aligned(f.out, 4 * f.n_pol))
+            return fail(FNT_ERR_INVALID, "frame %d: output must be %d-byte aligned", idx, 4 * f.n_pol);
+    } else {
+        df.n_sym = chain_nsym(f.n, df.phase);
+        if (!aligned(f.out, 4) || !aligned(f.aeq_state, 4))
+            return fail(FNT_ERR_INVALID, "frame %d: output and state must be 4-byte aligned", idx);
+    }
+    return FNT_OK;
+}
+
+static void add_cdc_items(const DevFrame &df, int fi, std::vector<int4> &items) {
+    const int64_t nblk = (df.n + df.S - 1) / df.S;
+    for (int64_t b = 0; b < nblk; b += kBlocksPerItem)
+        items.push_back(make_int4(fi, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), 0));
+}
+
+static void add_aeq_chains(const fnt_plan *p, const DevFrame &df, int fi, const int32_t *init_dev,
+                           std::vector<AeqChain> &chains) {
+    const int64_t n = df.n_sym;
+    if (n == 0) return;
+    const int64_t seg = p->d.aeq_segment;
+    if (seg <= 0 || seg >= n) {
+        AeqChain c{};
+        c.frame = fi;
+        c.write_state = df.state != nullptr;
+        c.begin = 0;
+        c.keep = 0;
+        c.end = n;
+        c.init = df.state ? df.state : init_dev;
+        chains.push_back(c);
+        return;
+    }
+    for (int64_t k = 0; k < n; k += seg) {
+        AeqChain c{};
+        c.frame = fi;
+        c.keep = k;
+        c.end = std::min(n, k + seg);
+        c.begin = std::max<int64_t>(0, k - p->d.aeq_warmup);
+        c.write_state = (df.state != nullptr) && c.end == n;
+        c.init = init_dev;
+        chains.push_back(c);
+    }
+}
+
+fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work &w) {
+    if (!b || b->n_frames < 0 || (b->n_frames > 0 && !b->frames))
+        return fail(FNT_ERR_INVALID, "bad frame batch");
+    w = Work();
+    w.op = op;
+    w.frames.resize(b->n_frames);
+    int64_t scratch = 0;
+    for (int i = 0; i < b->n_frames; ++i) {
+        fnt_status st = make_frame(p, b->frames[i], op, i, w.frames[i]);
+        if (st != FNT_OK) return st;
+        if (op == FNT_OP_CHAIN) {
+            w.scratch_off.push_back(scratch);
+            scratch += (w.frames[i].n_sym * 4 + 255) / 256 * 256;
+        }
+    }
+    w.scratch_bytes = scratch;
+    for (int i = 0; i < b->n_frames; ++i) {
+        if (op != FNT_OP_AEQ) add_cdc_items(w.frames[i], i, w.items);
+        if (op != FNT_OP_CDC) add_aeq_chains(p, w.frames[i], i, p->d_init, w.chains);
+    }
+    // longest chains first: they bound the makespan of the serial AEQ recurrences
+    std::stable_sort(w.chains.begin(), w.chains.end(), [](const AeqChain &a, const AeqChain &c) {
+        return (a.end - a.begin) > (c.end - c.begin);
+    });
+    if (w.items.size() > (size_t)INT32_MAX || w.chains.size() > (size_t)INT32_MAX)
+        return fail(FNT_ERR_INVALID, "batch too large");
+    return FNT_OK;
+}
+
+// Layout of one device allocation holding the tables and the intermediate buffer.
+void layout(Work &w) {
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    w.off_frames = 0;
+    w.off_items = up(w.off_frames + w.frames.size() * sizeof(DevFrame));
+    w.off_chains = up(w.off_items + w.items.size() * sizeof(int4));
+    w.off_scratch = up(w.off_chains + w.chains.size() * sizeof(AeqChain));
+    w.total = up(w.off_scratch + (size_t)w.scratch_bytes);
+    if (w.total == 0) w.total = 256;
+}
+
+// Points the chain frames' intermediate buffers into the allocation and copies
+// the three tables (host -> device, on `stream`).
+fnt_status upload_work(Work &w, char *dev, cudaStream_t stream) {
+    if (w.op == FNT_OP_CHAIN)
+        for (size_t i = 0; i < w.frames.size(); ++i)
+            w.frames[i].aeq_in = (int8_t *)(dev + w.off_scratch + w.scratch_off[i]);
+    cudaError_t e;
+    if (!w.frames.empty()) {
+        e = cudaMemcpyAsync(dev + w.off_frames, w.frames.data(), w.frames.size() * sizeof(DevFrame),
+                            cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "upload frames");
+    }
+    if (!w.items.empty()) {
+        e = cudaMemcpyAsync(dev + w.off_items, w.items.data(), w.items.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "upload items");
+    }
+    if (!w.chains.empty()) {
+        e = cudaMemcpyAsync(dev + w.off_chains, w.chains.data(), w.chains.size() * sizeof(AeqChain),
+                            cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "upload chains");
+    }
+    return FNT_OK;
+}
+
+int work_kernel_count(const Work &w) {
+    int k = 0;
+    if (w.op != FNT_OP_AEQ && !w.items.empty()) ++k;
+    if (w.op != FNT_OP_CDC && !w.chains.empty()) ++k;
+    return k;
+}
+
+fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream) {
+    const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
+    if (w.op != FNT_OP_AEQ && !w.items.empty()) {
+        const int nw = p->cdc_warps;
+        const int n = (int)w.items.size();
+        const int grid = std::min((n + nw - 1) / nw, p->n_sm * 64);
+        cudaError_t e = cdc_launch(frames, (const int4 *)(dev + w.off_items), n, w.op == FNT_OP_CHAIN, nw, grid,
+                                   stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cdc kernel launch");
+    }
+    if (w.op != FNT_OP_CDC && !w.chains.empty()) {
+        const int nw = p->aeq_warps;
+        const int n = (int)w.chains.size();
+        const int grid = (n + nw - 1) / nw;
+        AeqParams prm{p->d.mu_shift, p->d.rde_a};
+        cudaError_t e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(dev + w.off_chains), n, prm, nw, grid,
+                                   stream);
+        if (e != cudaSuccess) return cuda_fail(e, "aeq kernel launch");
+    }
+    return FNT_OK;
+}
+
+// Per-frame host<->device sizes for host_buffers = 1.
+static size_t in_bytes(const fnt_frame &f, int op) { return op == FNT_OP_AEQ ? f.n * 4 : f.n * 2 * f.n_pol; }
+
+static size_t out_bytes(const fnt_frame &f, int op, const DevFrame &df) {
+    if (op == FNT_OP_CDC) return f.n * 4 * f.n_pol;
+    if (op == FNT_OP_AEQ) return f.n * 8;
+    return df.n_sym * 8;
+}
+
+static fnt_status run(const fnt_plan *p, const fnt_frame_batch *b, int op, void *stream_) {
+    if (!p) return fail(FNT_ERR_INVALID, "null plan");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    Work w;
+    fnt_status st = build_work(p, b, op, w);
+    if (st != FNT_OK) return st;
+    layout(w);
+    // host buffers: device copies of every frame's in / out after the tables
+    std::vector<size_t> io_in, io_out;
+    size_t total = w.total;
+    if (b->host_buffers) {
+        for (int i = 0; i < b->n_frames; ++i) {
+            io_in.push_back(total);
+            total += (in_bytes(b->frames[i], op) + 255) / 256 * 256;
+            io_out.push_back(total);
+            total += (out_bytes(b->frames[i], op, w.frames[i]) + 255) / 256 * 256;
+        }
+    }
+    char *dev = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&dev, total, stream);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(FNT_ERR_NOMEM, "device memory") : cuda_fail(e, "cudaMallocAsync");
+    if (b->host_buffers) {
+        for (int i = 0; i < b->n_frames; ++i) {
+            const fnt_frame &f = b->frames[i];
+            DevFrame &df = w.frames[i];
+            df.in = (const int8_t *)(dev + io_in[i]);
+            df.out = dev + io_out[i];
+            if (op == FNT_OP_AEQ) df.aeq_in = (int8_t *)df.in;
+            const size_t nb = in_bytes(f, op);
+            if (nb) {
+                e = cudaMemcpyAsync(dev + io_in[i], f.in, nb, cudaMemcpyHostToDevice, stream);
+                if (e != cudaSuccess) { cudaFreeAsync(dev, stream); return cuda_fail(e, "copy input"); }
+            }
+        }
+    }
+    st = upload_work(w, dev, stream);
+    if (st == FNT_OK) st = launch_work(p, w, dev, stream);
+    if (st == FNT_OK && b->host_buffers) {
+        for (int i = 0; i < b->n_frames; ++i) {
+            const size_t nb = out_bytes(b->frames[i], op, w.frames[i]);
+            if (!nb) continue;
+            e = cudaMemcpyAsync(b->frames[i].out, dev + io_out[i], nb, cudaMemcpyDeviceToHost, stream);
+            if (e != cudaSuccess) { st = cuda_fail(e, "copy output"); break; }
+        }
+    }
+    cudaFreeAsync(dev, stream);
+    if (st == FNT_OK && b->host_buffers) {
+        e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+    }
+    return st;
+}
+
+}  // namespace fnt
+
+extern "C" fnt_status fnt_cdc_run(const fnt_plan *p, const fnt_frame_batch *b, void *stream) {
+    return run(p, b, FNT_OP_CDC, stream);
+}
+
+extern "C" fnt_status fnt_aeq_run(const fnt_plan *p, const fnt_frame_batch *b, void *stream) {
+    return run(p, b, FNT_OP_AEQ, stream);
+}
+
+extern "C" fnt_status fnt_cdc_aeq_run(const fnt_plan *p, const fnt_frame_batch *b, void *stream) {
+    return run(p, b, FNT_OP_CHAIN, stream);
+}
+
+// -------------------------------------------------------- prepared batches ---
+
+struct fnt_batch {
+    const fnt_plan *plan = nullptr;
+    Work work;
+    char *dev = nullptr;
+    int use_graph = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+};
+
+extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch *b, int32_t op, int32_t use_graph,
+                                       fnt_batch **out) {
+    if (!p || !out) return fail(FNT_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (op < FNT_OP_CDC || op > FNT_OP_CHAIN) return fail(FNT_ERR_INVALID, "unknown op %d", op);
+    if (b && b->host_buffers) return fail(FNT_ERR_INVALID, "fnt_batch needs device buffers");
+    fnt_batch *bt = new (std::nothrow) fnt_batch();
+    if (!bt) return fail(FNT_ERR_NOMEM, "host memory");
+    bt->plan = p;
+    bt->use_graph = use_graph;
+    fnt_status st = build_work(p, b, op, bt->work);
+    if (st != FNT_OK) {
+        delete bt;
+        return st;
+    }
+    layout(bt->work);
+    cudaError_t e = cudaMalloc((void **)&bt->dev, bt->work.total);
+    if (e != cudaSuccess) {
+        delete bt;
+        return e == cudaErrorMemoryAllocation ? fail(FNT_ERR_NOMEM, "device memory") : cuda_fail(e, "cudaMalloc");
+    }
+    st = upload_work(bt->work, bt->dev, 0);
+    if (st == FNT_OK) {
+        e = cudaStreamSynchronize(0);
+        if (e != cudaSuccess) st = cuda_fail(e, "upload sync");
+    }
+    if (st != FNT_OK) {
+        cudaFree(bt->dev);
+        delete bt;
+        return st;
+    }
+    *out = bt;
+    return FNT_OK;
+}
+
+extern "C" fnt_status fnt_batch_launch(fnt_batch *bt, void *stream_) {
+    if (!bt) return fail(FNT_ERR_INVALID, "null batch");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!bt->use_graph) return launch_work(bt->plan, bt->work, bt->dev, stream);
+    if (!bt->exec) {
+        cudaStream_t cap;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return cuda_fail(e, "cudaStreamBeginCapture");
+        }
+        fnt_status st = launch_work(bt->plan, bt->work, bt->dev, cap);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cap, &graph);
+        cudaStreamDestroy(cap);
+        if (st != FNT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&bt->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    cudaError_t e = cudaGraphLaunch(bt->exec, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return FNT_OK;
+}
+
+extern "C" int32_t fnt_batch_kernel_count(const fnt_batch *bt) { return bt ? work_kernel_count(bt->work) : 0; }
+
+extern "C" fnt_status fnt_batch_destroy(fnt_batch *bt) {
+    if (!bt) return FNT_OK;
+    cudaDeviceSynchronize();
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    cudaFree(bt->dev);
+    delete bt;
+    return FNT_OK;
+}

@@ -1,0 +1,214 @@
+// cdc.cu -- FNT-CDC kernel: overlap-save complex convolution through length-64
+// Fermat number transforms over Z_65537 with radix sqrt(2) = 4080 (section
+// "Proposed FNT-CDC&AEQ structure"; eqs. (1), (2), (5), (7), (8)).
+//
+// Work item = 32 consecutive overlap-save blocks of one frame, one warp; lane l
+// owns block b0 + l entirely in registers:
+//   u = x_re + 2^8 x_im, v = x_re - 2^8 x_im          (2^8 = sqrt(-1) mod F)
+//   P = FNT(u) . H_u,   Q = FNT(v) . H_v                (H = FNT of the taps,
+//                                                        times N^-1 2^-1)
+//   z_re = IFNT(P + Q),  z_im = IFNT(-2^8 (P - Q))       (eqs. (7) and (8))
+// By linearity FNT(u) = X + 2^8 Xh with X, Xh the transforms of the real and
+// imaginary parts, so this is eqs. (7)/(8) with two forward transforms instead
+// of four and the constants -2^15 = 2^-1 and -2^7 = 2^-9 folded into H.
+//
+// Memory path: each warp copies its 32 input windows (64 samples each, 16 B
+// loads coalesced) into a [position][lane] shared-memory transpose (33-word
+// rows: conflict-free for the column reads of the lanes and the row writes of
+// the fill), and writes results back through the same buffers with coalesced
+// 8-byte (CDC) or 4-byte (chain) stores.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "zf.cuh"
+
+namespace fnt {
+
+namespace {
+
+constexpr int kN = kCdcN;
+constexpr int64_t kAlpha = 4080;
+constexpr int kRow = 33;                                 // padded smem row (words)
+constexpr int kWarpWords = 2 * kN * kRow + 2 * kN;       // win, o0, H_u, H_v
+// N^-1 * 2^-1 folded into the tap spectra
+constexpr int32_t kHScale = zcent(zinv(kN) * zinv(2) % kF);
+
+__device__ __forceinline__ int32_t sx8(uint32_t w, int sh) { return (int32_t)(w << (24 - sh)) >> 24; }
+
+__device__ __forceinline__ int32_t sat5(int32_t v) { return v < -16 ? -16 : (v > 15 ? 15 : v); }
+
+// One block of one polarisation: window words w[j] = win[j][lane]; result
+// packed (re | im << 16) into o[j][lane] for all 64 window positions.
+// `o` may be `win` itself: every output depends on every input of the lane's
+// column, so all reads precede all writes.
+__device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, const int32_t *hs, int lane,
+                                          int sh) {
+    int32_t P[kN];
+#pragma unroll
+    for (int j = 0; j < kN; ++j) {
+        const uint32_t w = win[j * kRow + lane];
+        P[j] = sx8(w, sh) + 256 * sx8(w, sh + 8);
+    }
+    fnt_fwd<kN, kAlpha>(P);
+#pragma unroll
+    for (int i = 0; i < kN; ++i) P[i] = rho(rhoc(P[i]) * hs[i]);
+
+    int32_t Q[kN];
+#pragma unroll
+    for (int j = 0; j < kN; ++j) {
+        const uint32_t w = win[j * kRow + lane];
+        Q[j] = sx8(w, sh) - 256 * sx8(w, sh + 8);
+    }
+    fnt_fwd<kN, kAlpha>(Q);
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+        const int32_t q = rho(rhoc(Q[i]) * hs[kN + i]);
+        const int32_t a = P[i] + q;
+        const int32_t b = P[i] - q;
+        P[i] = rho(a);
+        Q[i] = rho(b * -256);
+    }
+    fnt_inv<kN, kAlpha>(P);
+#pragma unroll
+    for (int j = 0; j < kN; ++j) P[j] = decode(P[j]);
+    fnt_inv<kN, kAlpha>(Q);
+#pragma unroll
+    for (int j = 0; j < kN; ++j) {
+        const int32_t im = decode(Q[j]);
+        o[j * kRow + lane] = ((uint32_t)P[j] & 0xFFFFu) | ((uint32_t)im << 16);
+    }
+}
+
+template <bool CHAIN>
+__global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict__ frames,
+                                                     const int4 *__restrict__ items, int n_items) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int32_t s_pow[kN];
+    if (threadIdx.x < kN) s_pow[threadIdx.x] = zcent(zpow(kAlpha, threadIdx.x));
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    uint32_t *win = smem + warp * kWarpWords;     // [64][33] input words; pol-1 results
+    uint32_t *o0 = win + kN * kRow;               // [64][33] pol-0 results
+    int32_t *hs = (int32_t *)(o0 + kN * kRow);    // H_u [64], H_v [64] in bit-reversed order
+
+    for (int it = blockIdx.x * wpb + warp; it < n_items; it += gridDim.x * wpb) {
+        const int4 item = items[it];
+        const DevFrame &fr = frames[item.x];
+        const int64_t b0 = item.y;
+        const int nb = item.z;
+        const int S = fr.S;
+        const int L = fr.L;
+        const int npol = fr.n_pol;
+        const int64_t n = fr.n;
+
+        // Tap spectra H[k] = sum_n h[n] alpha^(nk), k = bitrev(i), lanes i and i + 32.
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = lane + 32 * h;
+            const int k = (int)(__brev((unsigned)i) >> 26);
+            int32_t au = 0, av = 0;
+            for (int m = 0; m < L; ++m) {
+                const int32_t hr = fr.taps[2 * m], hi = fr.taps[2 * m + 1];
+                const int32_t pw = s_pow[(m * k) & (kN - 1)];
+                au += rho((hr + 256 * hi) * pw);
+                av += rho((hr - 256 * hi) * pw);
+            }
+            hs[i] = rhoc(rho(rhoc(au) * kHScale));
+            hs[kN + i] = rhoc(rho(rhoc(av) * kHScale));
+        }
+
+        // Input windows: window l covers samples base + l*S + [0, 64).
+        const int64_t base = b0 * S - (kN - S);
+        const int esz = 2 * npol;
+        for (int l = 0; l < 32; ++l) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = lane + 32 * h;
+                const int64_t t = base + (int64_t)l * S + j;
+                uint32_t w = 0;
+                if (l < nb && t >= 0 && t < n) {
+                    w = npol == 2 ? __ldg((const uint32_t *)(fr.in + t * esz))
+                                  : (uint32_t)__ldg((const uint16_t *)(fr.in + t * esz));
+                }
+                win[j * kRow + l] = w;
+            }
+        }
+        __syncwarp();
+
+        cdc_block(win, o0, hs, lane, 0);
+        if (npol == 2) {
+            __syncwarp();
+            cdc_block(win, win, hs, lane, 16);   // each lane reads and writes only its own column
+        }
+        __syncwarp();
+
+        if (!CHAIN) {
+            int16_t *out = (int16_t *)fr.out;
+            for (int l = 0; l < nb; ++l) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int jj = lane + 32 * h;
+                    const int64_t t = (b0 + l) * S + jj;
+                    if (jj < S && t < n) {
+                        const int pos = (kN - S + jj) * kRow + l;
+                        if (npol == 2) {
+                            *(uint2 *)(out + t * 4) = make_uint2(o0[pos], win[pos]);
+                        } else {
+                            *(uint32_t *)(out + t * 2) = o0[pos];
+                        }
+                    }
+                }
+            }
+        } else {
+            // requantise to 5 bits and keep times t = phase (mod 2)
+            const int sft = fr.shift;
+            const int32_t rnd = sft > 0 ? (1 << (sft - 1)) : 0;
+            uint32_t *xa = (uint32_t *)fr.aeq_in;
+            for (int l = 0; l < nb; ++l) {
+                const int64_t t0 = (b0 + l) * S;
+                const int jj = (int)((t0 - fr.phase) & 1) + 2 * lane;
+                const int64_t t = t0 + jj;
+                if (jj < S && t < n) {
+                    const int pos = (kN - S + jj) * kRow + l;
+                    const uint32_t w0 = o0[pos], w1 = win[pos];
+                    const int32_t c0 = sat5(((int32_t)(int16_t)(w0 & 0xFFFF) + rnd) >> sft);
+                    const int32_t c1 = sat5((((int32_t)w0 >> 16) + rnd) >> sft);
+                    const int32_t c2 = sat5(((int32_t)(int16_t)(w1 & 0xFFFF) + rnd) >> sft);
+                    const int32_t c3 = sat5((((int32_t)w1 >> 16) + rnd) >> sft);
+                    xa[(t - fr.phase) >> 1] = (uint32_t)(c0 & 0xFF) | ((uint32_t)(c1 & 0xFF) << 8) |
+                                              ((uint32_t)(c2 & 0xFF) << 16) | ((uint32_t)c3 << 24);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+size_t cdc_smem_bytes(int warps) { return (size_t)warps * kWarpWords * sizeof(uint32_t); }
+
+cudaError_t cdc_configure() {
+    const size_t max_smem = cdc_smem_bytes(8);
+    cudaError_t e = cudaFuncSetAttribute(cdc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)max_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(cdc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+}
+
+cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, int warps,
+                       int grid, cudaStream_t stream) {
+    if (n_items <= 0) return cudaSuccess;
+    const dim3 block(32 * warps);
+    const size_t smem = cdc_smem_bytes(warps);
+    if (chain)
+        cdc_kernel<true><<<grid, block, smem, stream>>>(frames, items, n_items);
+    else
+        cdc_kernel<false><<<grid, block, smem, stream>>>(frames, items, n_items);
+    return cudaGetLastError();
+}
+
+}  // namespace fnt

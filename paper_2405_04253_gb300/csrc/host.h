@@ -1,0 +1,58 @@
+// host.h -- host-side declarations shared by the translation units of libfnt.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "fnt.h"
+#include "internal.h"
+
+struct fnt_plan {
+    fnt_plan_desc d;
+    int32_t h_init[16 * fnt::kAeqK];
+    int32_t *d_init = nullptr;   // device copy of the initial taps
+    int device = 0;
+    int n_sm = 1;
+    int cdc_warps = 4;
+    int aeq_warps = 4;
+};
+
+namespace fnt {
+
+fnt_status fail(fnt_status st, const char *fmt, ...);
+fnt_status cuda_fail(cudaError_t e, const char *what);
+
+int cdc_shift_of(const int8_t *taps, int L);
+int decim_phase_of(int L);
+int64_t chain_nsym(int64_t n, int phase);
+
+// Work lists of one call or prepared batch.
+struct Work {
+    int op = 0;
+    std::vector<DevFrame> frames;
+    std::vector<int4> items;          // CDC: (frame, first block, blocks)
+    std::vector<AeqChain> chains;     // AEQ runs, longest first
+    std::vector<int64_t> scratch_off; // chain: per-frame offset of the intermediate buffer
+    int64_t scratch_bytes = 0;
+    size_t off_frames = 0, off_items = 0, off_chains = 0, off_scratch = 0, total = 0;
+};
+
+fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work &w);
+void layout(Work &w);
+fnt_status upload_work(Work &w, char *dev, cudaStream_t stream);
+fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream);
+int work_kernel_count(const Work &w);
+
+// kernels
+size_t cdc_smem_bytes(int warps);
+cudaError_t cdc_configure();
+cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, int warps, int grid,
+                       cudaStream_t stream);
+size_t aeq_smem_bytes(int na, int warps);
+cudaError_t aeq_configure();
+cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,
+                       int warps, int grid, cudaStream_t stream);
+
+}  // namespace fnt

@@ -1,0 +1,47 @@
+// internal.h -- device-side work descriptors shared by the kernels and the host
+// side of libfnt (not part of the public C ABI).
+#pragma once
+
+#include <cstdint>
+
+namespace fnt {
+
+constexpr int kCdcN = 64;          // CDC transform length
+constexpr int kMaxCdTaps = 31;     // |Re z|, |Im z| <= 31 * 2 * 16 * 32 < 2^15 (eq. (5), int16 out)
+constexpr int kAeqK = 16;          // taps per real AEQ filter
+constexpr int kBlocksPerItem = 32; // CDC blocks per warp work item (one per lane)
+
+// One frame as the kernels see it (128 bytes, 16-byte aligned).
+struct alignas(16) DevFrame {
+    const int8_t *in;      // CDC / chain: int8 [n][n_pol][2]; AEQ alone: int8 [n][4]
+    void *out;             // CDC: int16 [n][n_pol][2]; chain / AEQ: int16 [n_sym][4]
+    int8_t *aeq_in;        // AEQ input int8 [n_sym][4] (chain: intermediate buffer)
+    int32_t *state;        // AEQ master taps [4][4][K] or nullptr
+    int64_t n;             // samples (CDC, chain) or symbols (AEQ alone)
+    int64_t n_sym;         // AEQ symbols
+    int32_t n_pol;
+    int32_t L;             // CD taps
+    int32_t S;             // CDC overlap-save step
+    int32_t shift;         // CDC -> AEQ requantisation shift s_c
+    int32_t phase;         // decimation phase
+    int32_t pad0;
+    int8_t taps[64];       // [L][2] (re, im), zero beyond L
+};
+static_assert(sizeof(DevFrame) == 128 + 0 || sizeof(DevFrame) % 16 == 0, "DevFrame layout");
+
+// One AEQ run: a whole frame, or one segment of a long frame.
+struct alignas(16) AeqChain {
+    int32_t frame;
+    int32_t write_state;   // 1: write the final taps to the frame's state
+    int64_t begin;         // first symbol the run processes (history is zero before it)
+    int64_t keep;          // first symbol whose output is stored
+    int64_t end;           // one past the last symbol
+    const int32_t *init;   // initial taps (frame state or the plan's initial taps)
+};
+
+struct AeqParams {
+    int32_t mu_shift;
+    int32_t rde_a;
+};
+
+}  // namespace fnt

@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element
+by element on seeded inputs.  Every comparison is bit-exact (integer work)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2405_04253_gb300 as F  # noqa: E402
+import synth  # noqa: E402
+
+
+def dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def i16(shape):
+    return torch.full(shape, 0x5A5A, dtype=torch.int16, device="cuda")   # poison
+
+
+def run_cdc(plan, x, taps):
+    xd = dev(x)
+    out = i16((x.shape[0], x.shape[1], 2))
+    F.cdc_run(plan, [F.Frame(xd, out, taps, n_pol=x.shape[1])])
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.int32)
+
+
+# --------------------------------------------------------------------- CDC -----
+
+CDC_CASES = [(1000, 1, 17), (777, 2, 19), (3000, 2, 5), (64, 1, 17), (47, 2, 17), (1, 2, 17),
+             (0, 2, 17), (333, 1, 1), (5000, 2, 31), (48 * 32 * 3 + 7, 2, 17), (20000, 2, 12)]
+
+
+@pytest.mark.parametrize("n,n_pol,L", CDC_CASES)
+def test_cdc_random_matches_oracle(orc, n, n_pol, L):
+    rng = np.random.default_rng(100 + n + L)
+    x = rng.integers(-16, 16, (n, n_pol, 2)).astype(np.int8)
+    taps = rng.integers(-32, 32, (L, 2)).astype(np.int8)
+    plan = F.Plan()
+    got = run_cdc(plan, x, taps)
+    assert np.array_equal(got, orc.cdc(x, taps) if n else np.zeros((0, n_pol, 2), np.int32))
+
+
+@pytest.mark.parametrize("step", [32, 40, 48])
+def test_cdc_custom_step(orc, step):
+    rng = np.random.default_rng(step)
+    x = rng.integers(-16, 16, (4000, 2, 2)).astype(np.int8)
+    taps = rng.integers(-32, 32, (17, 2)).astype(np.int8)
+    got = run_cdc(F.Plan(cdc_step=step), x, taps)
+    assert np.array_equal(got, orc.cdc(x, taps, 64, 4080, step))
+
+
+def test_cdc_extremes(orc):
+    n = 4096
+    for xv, hv in [(-16, -32), (15, 31), (-16, 31), (-1, -1)]:
+        x = np.full((n, 2, 2), xv, dtype=np.int8)
+        x[::7, 1, 0] = -xv - 1 if xv < 15 else -16
+        taps = np.full((31, 2), hv, dtype=np.int8)
+        got = run_cdc(F.Plan(), x, taps)
+        assert np.array_equal(got, orc.cdc(x, taps))
+
+
+def test_cdc_synthetic_config1(orc):
+    f = synth.config1()
+    got = run_cdc(F.Plan(), f.x, f.taps)
+    assert np.array_equal(got, orc.cdc(f.x, f.taps))
+
+
+def test_cdc_batch_of_mixed_frames(orc):
+    rng = np.random.default_rng(77)
+    plan = F.Plan()
+    frames, refs = [], []
+    for i in range(9):
+        n = int(rng.integers(0, 9000))
+        npol = int(rng.integers(1, 3))
+        L = int(rng.integers(1, 32))
+        x = rng.integers(-16, 16, (n, npol, 2)).astype(np.int8)
+        taps = rng.integers(-32, 32, (L, 2)).astype(np.int8)
+        out = i16((n, npol, 2))
+        frames.append(F.Frame(dev(x), out, taps, n_pol=npol))
+        refs.append(orc.cdc(x, taps) if n else np.zeros((0, npol, 2), np.int32))
+    F.cdc_run(plan, frames)
+    torch.cuda.synchronize()
+    for fr, ref in zip(frames, refs):
+        assert np.array_equal(fr.out.cpu().numpy().astype(np.int32), ref)
+
+
+def test_cdc_rejects_bad_frames():
+    plan = F.Plan()
+    x = torch.zeros((100, 2, 2), dtype=torch.int8, device="cuda")
+    out = i16((100, 2, 2))
+    with pytest.raises(F.FntError) as e:
+        F.cdc_run(plan, [F.Frame(x, out, np.zeros((32, 2), np.int8))])
+    assert e.value.status == F.FNT_ERR_BOUND
+    with pytest.raises(F.FntError) as e:
+        F.cdc_run(plan, [F.Frame(x, out, np.full((5, 2), 40, np.int8))])
+    assert e.value.status == F.FNT_ERR_INVALID
+    with pytest.raises(F.FntError):
+        F.Plan(alpha_cdc=2)          # order 32, not 64: eq. (4) fails
+
+
+# --------------------------------------------------------------------- AEQ -----
+
+def run_aeq(plan, x, T=None):
+    xd = dev(x)
+    out = i16((x.shape[0], 4))
+    st = None if T is None else dev(T)
+    F.aeq_run(plan, [F.Frame(xd, out, state=st)])
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), (None if st is None else st.cpu().numpy())
+
+
+@pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
+@pytest.mark.parametrize("n,mu", [(1000, 8), (333, 12), (16, 8), (5, 8), (2000, 63), (4096 + 3, 6)])
+def test_aeq_matches_oracle(orc, na, alpha, n, mu):
+    rng = np.random.default_rng(na * 1000 + n + mu)
+    x = rng.integers(-16, 16, (n, 4)).astype(np.int8)
+    T0 = orc.aeq_init_taps(16, 2048)
+    T0 = T0 + rng.integers(-(1 << 20), 1 << 20, T0.shape).astype(np.int32)
+    plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=mu, rde_a=64)
+    got, Tg = run_aeq(plan, x, T0)
+    ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=mu, rde_a=64)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(Tg, Tr)
+
+
+@pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
+def test_aeq_extreme_taps(orc, na, alpha):
+    rng = np.random.default_rng(3)
+    x = np.full((700, 4), -16, dtype=np.int8)
+    x[::3] = 15
+    W = rng.choice([-8192, 8191, -1, 0, 127, -128], size=(4, 4, 16)).astype(np.int64)
+    T0 = (W << 16).astype(np.int32)
+    plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=30, rde_a=4096)
+    got, Tg = run_aeq(plan, x, T0)
+    ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=30, rde_a=4096)
+    assert np.array_equal(got, ref) and np.array_equal(Tg, Tr)
+
+
+def test_aeq_no_state_uses_plan_init(orc):
+    rng = np.random.default_rng(4)
+    x = rng.integers(-16, 16, (900, 4)).astype(np.int8)
+    plan = F.Plan(mu_shift=9, tap_init=3000)
+    got, _ = run_aeq(plan, x, None)
+    ref, _ = orc.aeq(x, orc.aeq_init_taps(16, 3000), 32, 2, mu_shift=9, rde_a=64)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
+def test_aeq_segmented_matches_oracle(orc, na, alpha):
+    rng = np.random.default_rng(5)
+    x = rng.integers(-16, 16, (5000, 4)).astype(np.int8)
+    plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=9, aeq_segment=700, aeq_warmup=150)
+    T = np.zeros((4, 4, 16), np.int32)
+    got, Tg = run_aeq(plan, x, T)
+    ref, Tr = orc.aeq_segmented(x, orc.aeq_init_taps(16, 2048), na, alpha, mu_shift=9, rde_a=64,
+                                seg_len=700, warmup=150)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(Tg, Tr)
+
+
+# ------------------------------------------------------------------- chain -----
+
+def oracle_chain(orc, x, taps, **kw):
+    prm = orc.ChainParams(**kw)
+    return orc.chain(x, taps, prm)
+
+
+@pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
+def test_chain_synthetic_matches_oracle(orc, na, alpha):
+    f = synth.config2(1 << 12)
+    plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=9)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    out = i16((nsym, 4))
+    st = dev(np.zeros((4, 4, 16), np.int32))
+    st.copy_(dev(orc.aeq_init_taps(16, 2048)))
+    F.cdc_aeq_run(plan, [F.Frame(dev(f.x), out, f.taps, st)])
+    torch.cuda.synchronize()
+    ref, Tr = oracle_chain(orc, f.x, f.taps, n_aeq=na, alpha_aeq=alpha, mu_shift=9)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    assert np.array_equal(st.cpu().numpy(), Tr)
+
+
+def test_chain_batch_mixed_lengths_and_taps(orc):
+    rng = np.random.default_rng(8)
+    plan = F.Plan(mu_shift=9)
+    frames, refs = [], []
+    for i in range(7):
+        n = int(rng.integers(0, 6000))
+        L = int(rng.choice([5, 7, 9, 17, 19, 31]))
+        x = rng.integers(-16, 16, (n, 2, 2)).astype(np.int8)
+        taps = rng.integers(-32, 32, (L, 2)).astype(np.int8)
+        out = i16((F.chain_nsym(n, L), 4))
+        frames.append(F.Frame(dev(x), out, taps))
+        refs.append(oracle_chain(orc, x, taps, mu_shift=9)[0])
+    F.cdc_aeq_run(plan, frames)
+    torch.cuda.synchronize()
+    for fr, ref in zip(frames, refs):
+        assert np.array_equal(fr.out.cpu().numpy(), ref)
+
+
+def test_chain_segmented_and_prepared_batch(orc):
+    f = synth.config2(1 << 13)
+    kw = dict(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=1024, aeq_warmup=256)
+    plan = F.Plan(**kw)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    out1 = i16((nsym, 4))
+    out2 = i16((nsym, 4))
+    xd = dev(f.x)
+    F.cdc_aeq_run(plan, [F.Frame(xd, out1, f.taps)])
+    b = F.Batch(plan, [F.Frame(xd, out2, f.taps)], F.OP_CHAIN, use_graph=True)
+    b.launch()
+    b.launch()
+    torch.cuda.synchronize()
+    ref, _ = oracle_chain(orc, f.x, f.taps, seg_len=1024, warmup=256, **{k: v for k, v in kw.items()
+                                                                         if k in ("n_aeq", "alpha_aeq", "mu_shift")})
+    assert np.array_equal(out1.cpu().numpy(), ref)
+    assert np.array_equal(out2.cpu().numpy(), ref)
+    assert b.kernel_count() == 2
+
+
+def test_chain_host_buffers_equal_device(orc):
+    f = synth.config2(1 << 12)
+    plan = F.Plan(mu_shift=9)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    host_out = np.zeros((nsym, 4), np.int16)
+    F.cdc_aeq_run(plan, [F.Frame(np.ascontiguousarray(f.x), host_out, f.taps)], host=True)
+    ref, _ = oracle_chain(orc, f.x, f.taps, mu_shift=9)
+    assert np.array_equal(host_out, ref)
