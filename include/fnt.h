@@ -205,6 +205,12 @@ FNT_API fnt_status fnt_batch_create(const fnt_plan *plan, const fnt_frame_batch 
  * overlap on the device (they share its intermediate buffers). */
 FNT_API fnt_status fnt_batch_launch(fnt_batch *b, void *stream);
 
+/* Enqueues one stage of the prepared work: stage 0 = the CDC kernel, stage 1 =
+ * the AEQ kernel (a stage the op does not have enqueues nothing).  Running
+ * stage 0 then stage 1 on one stream equals fnt_batch_launch without a graph;
+ * it lets a caller time or overlap the two kernels separately. */
+FNT_API fnt_status fnt_batch_launch_stage(fnt_batch *b, int32_t stage, void *stream);
+
 /* Number of kernel launches one fnt_batch_launch enqueues. */
 FNT_API int32_t fnt_batch_kernel_count(const fnt_batch *b);
 
@@ -269,7 +275,13 @@ FNT_API int32_t fnt_session_pending(const fnt_session *s);
 FNT_API fnt_status fnt_session_get_link_state(fnt_session *s, int32_t link, int32_t *state);
 FNT_API fnt_status fnt_session_set_link_state(fnt_session *s, int32_t link, const int32_t *state);
 
-/* Waits for every admitted request, then frees the session. */
+/* Fault injection for tests of the serving loop (host side only): the next
+ * n_waves wave launches fail before anything is enqueued, as a failed CUDA call
+ * would; their requests complete with status FNT_ERR_CUDA, their memory is
+ * released and their links' tap states are left as they were. */
+FNT_API fnt_status fnt_session_inject_failures(fnt_session *s, int32_t n_waves);
+
+/* Runs every admitted request to completion, then frees the session. */
 FNT_API fnt_status fnt_session_destroy(fnt_session *s);
 
 #ifdef __cplusplus

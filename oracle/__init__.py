@@ -235,3 +235,27 @@ def chain(x: np.ndarray, taps: np.ndarray, prm: ChainParams, T0: np.ndarray | No
         return aeq_segmented(xa, T0, prm.n_aeq, prm.alpha_aeq, prm.mu_shift, prm.rde_a,
                              prm.seg_len, prm.warmup, use_fnt)
     return aeq(xa, T0, prm.n_aeq, prm.alpha_aeq, prm.mu_shift, prm.rde_a, use_fnt)
+
+
+def chain_segment(x: np.ndarray, taps: np.ndarray, prm: ChainParams, seg: int, T0: np.ndarray | None = None):
+    """Outputs of AEQ segment `seg` of the segmented chain, computed from the
+    input slice it depends on alone (so a long stream can be checked at sampled
+    segments).  Returns (first symbol, out int16 [m, 4], final taps)."""
+    n = x.shape[0]
+    L = taps.shape[0]
+    phase = decim_phase(L)
+    n_sym = max(0, (n - phase + 1) // 2)
+    seg_len = prm.seg_len if prm.seg_len > 0 else max(1, n_sym)
+    keep = seg * seg_len
+    end = min(n_sym, keep + seg_len)
+    begin = max(0, keep - prm.warmup) if prm.seg_len > 0 else 0
+    t_lo = 2 * begin + phase                      # first 2-sps time the segment reads
+    t_hi = 2 * (end - 1) + phase + 1
+    s0 = max(0, t_lo - (L - 1))                   # CDC history of the first output
+    z = cdc(x[s0:t_hi], taps, prm.n_cdc, prm.alpha_cdc)
+    xa = requant_decimate(z[t_lo - s0:], cdc_shift(taps), 0)
+    assert xa.shape[0] == end - begin
+    if T0 is None:
+        T0 = aeq_init_taps(prm.aeq_taps, prm.w0)
+    out, T = aeq(xa, T0, prm.n_aeq, prm.alpha_aeq, prm.mu_shift, prm.rde_a)
+    return keep, out[keep - begin:], T

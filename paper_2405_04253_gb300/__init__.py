@@ -66,6 +66,7 @@ SIGNATURES = {
     "fnt_cdc_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
     "fnt_batch_create": (_I32, [_VP, ctypes.POINTER(BatchC), _I32, _I32, ctypes.POINTER(_VP)]),
     "fnt_batch_launch": (_I32, [_VP, _VP]),
+    "fnt_batch_launch_stage": (_I32, [_VP, _I32, _VP]),
     "fnt_batch_kernel_count": (_I32, [_VP]),
     "fnt_batch_destroy": (_I32, [_VP]),
     "fnt_session_create": (_I32, [_VP, _I32, _SZ, _I32, ctypes.POINTER(_VP)]),
@@ -75,6 +76,7 @@ SIGNATURES = {
     "fnt_session_pending": (_I32, [_VP]),
     "fnt_session_get_link_state": (_I32, [_VP, _I32, _VP]),
     "fnt_session_set_link_state": (_I32, [_VP, _I32, _VP]),
+    "fnt_session_inject_failures": (_I32, [_VP, _I32]),
     "fnt_session_destroy": (_I32, [_VP]),
 }
 
@@ -88,10 +90,9 @@ def lib(path: str | None = None):
         p = path or os.environ.get("FNT_LIB") or build()
         L = ctypes.CDLL(p)
         for name, (res, args) in SIGNATURES.items():
-            if hasattr(L, name):
-                fn = getattr(L, name)
-                fn.restype = res
-                fn.argtypes = args
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
         _lib = L
     return _lib
 
@@ -206,6 +207,9 @@ class Batch:
     def launch(self, stream=None):
         check(lib().fnt_batch_launch(self.handle, _stream_handle(stream)))
 
+    def launch_stage(self, stage: int, stream=None):
+        check(lib().fnt_batch_launch_stage(self.handle, stage, _stream_handle(stream)))
+
     def kernel_count(self) -> int:
         return int(lib().fnt_batch_kernel_count(self.handle))
 
@@ -225,3 +229,79 @@ def chain_nsym(n: int, L: int) -> int:
     """Symbols the chain writes for n samples and L CD taps."""
     phase = ((L - 1) // 2) & 1
     return max(0, (n - phase + 1) // 2)
+
+
+class Session:
+    """Continuous-batching serving session (fnt_session)."""
+
+    def __init__(self, plan: Plan, n_links: int, mem_cap_bytes: int, n_streams: int = 4):
+        self.plan = plan
+        h = ctypes.c_void_p()
+        check(lib().fnt_session_create(plan.handle, n_links, mem_cap_bytes, n_streams, ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def set_link(self, link: int, taps):
+        t = np.ascontiguousarray(taps, dtype=np.int8)
+        check(lib().fnt_session_set_link(self.handle, link, t.ctypes.data, t.shape[0]))
+
+    def submit(self, link: int, x, out, n: int | None = None) -> int:
+        """Returns the ticket; raises FntError (status FNT_ERR_BUSY) when the
+        memory cap refuses admission."""
+        tk = ctypes.c_uint64()
+        check(lib().fnt_session_submit(self.handle, link, _ptr(x), int(x.shape[0]) if n is None else int(n),
+                                       _ptr(out), ctypes.byref(tk)))
+        self._keep[tk.value] = (x, out)
+        return tk.value
+
+    def try_submit(self, link: int, x, out, n: int | None = None) -> int | None:
+        tk = ctypes.c_uint64()
+        st = lib().fnt_session_submit(self.handle, link, _ptr(x), int(x.shape[0]) if n is None else int(n),
+                                      _ptr(out), ctypes.byref(tk))
+        if st == FNT_ERR_BUSY:
+            return None
+        check(st)
+        self._keep[tk.value] = (x, out)
+        return tk.value
+
+    def poll(self, timeout_us: int = 0, max_done: int = 1024):
+        arr = (Completion * max_done)()
+        nd = ctypes.c_int32()
+        st = lib().fnt_session_poll(self.handle, timeout_us, arr, max_done, ctypes.byref(nd))
+        if st == FNT_ERR_TIMEOUT:
+            return []
+        check(st)
+        out = []
+        for i in range(nd.value):
+            c = arr[i]
+            self._keep.pop(c.ticket, None)
+            out.append(dict(ticket=c.ticket, link=c.link, status=c.status, n_sym=c.n_sym, submit_us=c.submit_us,
+                            start_us=c.start_us, done_us=c.done_us))
+        return out
+
+    def pending(self) -> int:
+        return int(lib().fnt_session_pending(self.handle))
+
+    def get_link_state(self, link: int) -> np.ndarray:
+        st = np.zeros((4, 4, 16), np.int32)
+        check(lib().fnt_session_get_link_state(self.handle, link, st.ctypes.data))
+        return st
+
+    def set_link_state(self, link: int, state):
+        st = np.ascontiguousarray(state, dtype=np.int32)
+        check(lib().fnt_session_set_link_state(self.handle, link, st.ctypes.data))
+
+    def inject_failures(self, n_waves: int):
+        check(lib().fnt_session_inject_failures(self.handle, n_waves))
+
+    def close(self):
+        if self.handle:
+            lib().fnt_session_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -2,21 +2,26 @@
 // groups and the RDE tap update of eq. (6) (section "Proposed FNT-CDC&AEQ
 // structure"), over Z_65537 with N = 32 / radix 2 or N = 64 / radix 4080.
 //
-// One warp runs one AEQ chain (a frame, or one segment of a long frame).  The
-// tap update makes consecutive blocks of a chain a serial recurrence, so the
-// parallelism inside a block is spread over the lanes:
-//   lane = 16 p + 8 o + 2 s1 + g   (p: output polarisation, S2 = 2p + o,
-//                                   s1: input stream, g: tap group hi / lo)
-// Each lane owns the 16 master taps of filter S1 -> S2 in registers and, per
-// block, runs the forward transform of its tap group, the product with the
-// block's input spectrum, and the inverse transform -- one length-N transform
-// pair per lane, 32 per block, as in the paper's per-pair convolution.  The
-// four input spectra of 8 blocks at a time are computed by the 32 lanes
-// together (one transform each) ahead of use, since they do not depend on the
-// taps.  Results are combined through shared memory: y_S2 = sum over S1 of
-// 128 c_hi + c_lo, z = sat16(y >> 7), e = R - |z|^2 per polarisation, then each
-// lane accumulates the gradient of its 8 taps and the two lanes of a filter
-// swap halves so both hold all 16 updated taps.
+// Work item = one AEQ chain (a frame, or one segment of a long frame) and one
+// output polarisation p: the outputs S2 = 2p, 2p+1 depend on the shared input
+// but not on each other's taps, so the two polarisations of a chain are
+// independent recurrences and run in two warps.  Inside a warp,
+//   lane = 2 t + h,   t = 8 o + 2 s1 + g   (o: output of the pair, s1: input
+//                                           stream, g: tap group hi / lo)
+// and the length-N transform pair of task t is split over its two lanes by
+// even / odd frequency (h = frequency parity):
+//   forward  X[2k'+h] = FNT_{N/2, alpha^2}( a_j + a_{j+N/2}            (h = 0)
+//                                           (a_j - a_{j+N/2}) alpha^j ) (h = 1)
+//   inverse  x[n']       = E0[n'] + alpha^-n' E1[n']
+//            x[n' + N/2] = E0[n'] - alpha^-n' E1[n'],  E_h = IFNT_{N/2, alpha^2}(half h)
+// so each lane runs ordinary N/2-point transforms with compile-time twiddles
+// and one shuffle per output finishes the inverse.  The zero-padded taps sit in
+// the first half, so the forward split needs no shuffle at all.
+// Each lane holds the 16 master taps of its filter S1 -> S2 (all four lanes of
+// a filter hold them), accumulates the gradient of 4 of them, and the four
+// lanes swap their updated quarters.  The input spectra (taps-independent) are
+// computed 8 blocks ahead, one full N-point transform per lane, with N^-1
+// folded in.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -26,30 +31,58 @@ namespace fnt {
 
 namespace {
 
-template <int NA>
+template <int NA, int64_t ALPHA>
 struct AeqCfg {
     static constexpr int K = kAeqK;
+    static constexpr int M = NA / 2;                         // values per lane
     static constexpr int SA = NA - K;                        // symbols per block
     static constexpr int PRE = 8;                            // blocks per input-spectrum batch
     static constexpr int XS = PRE * SA + K;                  // staged input symbols (char4 words)
-    static constexpr int XF_ROW = NA + 1;
-    static constexpr int XF = PRE * 4 * XF_ROW;              // input spectra [PRE][4][NA]
+    static constexpr int HALF = M + 1;                       // padded half row
+    static constexpr int XF_ROW = 2 * HALF + 1;              // conflict-free: rows 3 banks apart
+    static constexpr int XF = PRE * 4 * XF_ROW;              // input spectra [PRE][4][2][M]
     static constexpr int RED_ROW = SA + 1;
-    static constexpr int RED = 32 * RED_ROW;                 // per-lane weighted outputs
-    static constexpr int ZS = 4 * SA;
-    static constexpr int ES = 2 * SA;
+    static constexpr int RED = 16 * RED_ROW;                 // per-task weighted outputs
+    static constexpr int ZS = 2 * SA;
+    static constexpr int ES = SA;
     static constexpr int WORDS = XS + XF + RED + ZS + ES;
     static constexpr int32_t NINV = zcent(zinv(NA));
+    static constexpr int64_t ALPHA2 = ALPHA * ALPHA % kF;    // radix of the half transforms
+    static constexpr int64_t AINV = zinv(ALPHA);
 };
 
 __device__ __forceinline__ int32_t sx8(uint32_t w, int sh) { return (int32_t)(w << (24 - sh)) >> 24; }
 
+// Lane h = 1 of the forward split: (a_j - 0) * alpha^j for the zero-padded taps.
+template <int NA, int64_t ALPHA, int J>
+struct SplitTaps {
+    static __device__ __forceinline__ void run(int32_t (&x)[NA / 2], const int32_t (&w)[kAeqK], bool odd) {
+        constexpr int32_t W = TwTab<NA, ALPHA>::tab.w[J];
+        x[J] = odd ? mulc<W>(w[J]) : w[J];
+        if constexpr (J + 1 < kAeqK) SplitTaps<NA, ALPHA, J + 1>::run(x, w, odd);
+    }
+};
+
+// Last inverse stage: lane 0 holds E0, lane 1 holds E1 (natural order); output
+// n' (lane 0) / n' + N/2 (lane 1) for n' >= FROM, decoded, into `res`.
+template <int NA, int64_t AINV, int J, int FROM>
+struct JoinHalves {
+    static __device__ __forceinline__ void run(const int32_t (&x)[NA / 2], int32_t (&res)[NA / 2], bool odd) {
+        constexpr int32_t W = TwTab<NA, AINV>::tab.w[J];
+        const int32_t t = odd ? mulc<W>(x[J]) : x[J];             // lane 1 sends alpha^-n' E1[n']
+        const int32_t r = __shfl_xor_sync(0xffffffffu, t, 1);
+        res[J] = rhoc(odd ? r - t : t + r);                       // |true value| <= 32512
+        if constexpr (J + 1 < NA / 2) JoinHalves<NA, AINV, J + 1, FROM>::run(x, res, odd);
+    }
+};
+
 template <int NA, int64_t ALPHA>
 __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ frames,
-                                                  const AeqChain *__restrict__ chains, int n_chains,
+                                                  const AeqChain *__restrict__ chains, int n_items,
                                                   AeqParams prm) {
-    using C = AeqCfg<NA>;
+    using C = AeqCfg<NA, ALPHA>;
     constexpr int K = C::K;
+    constexpr int M = C::M;
     constexpr int SA = C::SA;
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
@@ -61,15 +94,20 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
     int32_t *zs = red + C::RED;
     int32_t *es = zs + C::ZS;
 
-    const int p = lane >> 4;
-    const int s2 = 2 * p + ((lane >> 3) & 1);
-    const int s1 = (lane >> 1) & 3;
-    const int g = lane & 1;                   // 0: hi group (weight 128), 1: lo group
+    const int h = lane & 1;                   // frequency parity held by this lane
+    const int task = lane >> 1;
+    const int o = task >> 3;                  // output within the polarisation pair
+    const int s1 = (task >> 1) & 3;
+    const int g = task & 1;                   // 0: hi group (weight 128), 1: lo group
+    const int k0 = 8 * g + 4 * h;             // this lane's 4 gradient taps
+    const bool odd = h != 0;
     const int64_t A2 = (int64_t)prm.rde_a * prm.rde_a;
     const int mu = prm.mu_shift;
 
-    for (int c = blockIdx.x * wpb + warp; c < n_chains; c += gridDim.x * wpb) {
-        const AeqChain ch = chains[c];
+    for (int item = blockIdx.x * wpb + warp; item < n_items; item += gridDim.x * wpb) {
+        const AeqChain ch = chains[item >> 1];
+        const int p = item & 1;
+        const int s2 = 2 * p + o;
         const DevFrame &fr = frames[ch.frame];
         const uint32_t *xin = (const uint32_t *)fr.aeq_in;
         int16_t *out = (int16_t *)fr.out;
@@ -84,13 +122,14 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
             const int64_t t0 = ch.begin + blk * SA;
             if (bb == 0) {
                 __syncwarp();
-                // symbols t0 - K + q of the next PRE blocks, zero outside [begin, end)
                 for (int q = lane; q < C::XS; q += 32) {
                     const int64_t t = t0 - K + q;
                     xs[q] = (t >= ch.begin && t < ch.end) ? __ldg(xin + t) : 0u;
                 }
                 __syncwarp();
                 {
+                    // full N-point spectrum of input sq for block bq, N^-1 folded in;
+                    // register r = hh * M + j holds X[bitrev(r)] = X[2 bitrev_M(j) + hh]
                     const int bq = lane >> 2, sq = lane & 3;
                     int32_t x[NA];
 #pragma unroll
@@ -98,86 +137,111 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                     fnt_fwd<NA, ALPHA>(x);
                     int32_t *row = xf + (bq * 4 + sq) * C::XF_ROW;
 #pragma unroll
-                    for (int i = 0; i < NA; ++i) row[i] = rhoc(rho(rhoc(x[i]) * C::NINV));
+                    for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+                        for (int j = 0; j < M; ++j)
+                            row[hh * C::HALF + j] = rhoc(rho(rhoc(x[hh * M + j]) * C::NINV));
                 }
                 __syncwarp();
             }
 
-            // this lane's tap group, zero-padded to NA, through the transform pair
-            int32_t y[NA];
+            // tap group -> even / odd half spectrum in this lane
+            int32_t wv[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int32_t W = T[k] >> 16;
-                y[k] = g ? (W & 127) : (W >> 7);
+                wv[k] = g ? (W & 127) : (W >> 7);
             }
+            int32_t y[M];
+            SplitTaps<NA, ALPHA, 0>::run(y, wv, odd);
 #pragma unroll
-            for (int k = K; k < NA; ++k) y[k] = 0;
-            fnt_fwd_halfzero<NA, ALPHA>(y);
-            const int32_t *xrow = xf + (bb * 4 + s1) * C::XF_ROW;
+            for (int j = K; j < M; ++j) y[j] = 0;
+            if constexpr (M >= 2 * K)
+                fnt_fwd_halfzero<M, C::ALPHA2>(y);
+            else
+                fnt_fwd<M, C::ALPHA2>(y);
+            const int32_t *xrow = xf + (bb * 4 + s1) * C::XF_ROW + h * C::HALF;
 #pragma unroll
-            for (int i = 0; i < NA; ++i) y[i] = rho(rhoc(y[i]) * xrow[i]);
-            fnt_inv<NA, ALPHA>(y);
-            const int32_t wgt = g ? 1 : 128;
+            for (int j = 0; j < M; ++j) y[j] = rho(rhoc(y[j]) * xrow[j]);
+            fnt_inv<M, C::ALPHA2>(y);
+            int32_t c[M];
+            JoinHalves<NA, C::AINV, 0, 0>::run(y, c, odd);
+            {
+                // outputs n = h*M + j for n in [K, NA) -> block position i = n - K
+                const int32_t wgt = g ? 1 : 128;
+                int32_t *rrow = red + task * C::RED_ROW;
 #pragma unroll
-            for (int i = 0; i < SA; ++i) red[lane * C::RED_ROW + i] = decode(y[K + i]) * wgt;
+                for (int j = 0; j < M; ++j) {
+                    const int i = h * M + j - K;          // runtime in h only
+                    if (i >= 0) rrow[i] = c[j] * wgt;
+                }
+            }
             __syncwarp();
 
-            // outputs, RDE error
-            for (int q = lane; q < 2 * SA; q += 32) {
-                const int pp = q >= SA ? 1 : 0;
-                const int i = q - pp * SA;
-                int32_t z0, z1;
-                {
-                    int32_t a0 = 0, a1 = 0;
+            // outputs and RDE error of this polarisation
+            for (int i = lane; i < SA; i += 32) {
+                int32_t a0 = 0, a1 = 0;
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        a0 += red[(16 * pp + m) * C::RED_ROW + i];
-                        a1 += red[(16 * pp + 8 + m) * C::RED_ROW + i];
-                    }
-                    z0 = min(max(a0 >> 7, -32768), 32767);
-                    z1 = min(max(a1 >> 7, -32768), 32767);
+                for (int m = 0; m < 8; ++m) {
+                    a0 += red[m * C::RED_ROW + i];
+                    a1 += red[(8 + m) * C::RED_ROW + i];
                 }
+                const int32_t z0 = min(max(a0 >> 7, -32768), 32767);
+                const int32_t z1 = min(max(a1 >> 7, -32768), 32767);
                 const int64_t t = t0 + i;
                 const bool valid = t < ch.end;
                 const int64_t r2 = (int64_t)z0 * z0 + (int64_t)z1 * z1;
                 const int64_t R = r2 < 6 * A2 ? 2 * A2 : (r2 < 14 * A2 ? 10 * A2 : 18 * A2);
                 if (valid && t >= ch.keep)
-                    *(uint32_t *)(out + t * 4 + 2 * pp) = ((uint32_t)z0 & 0xFFFFu) | ((uint32_t)z1 << 16);
-                zs[(2 * pp) * SA + i] = valid ? z0 : 0;
-                zs[(2 * pp + 1) * SA + i] = valid ? z1 : 0;
-                es[pp * SA + i] = valid ? (int32_t)(R - r2) : 0;
+                    *(uint32_t *)(out + t * 4 + 2 * p) = ((uint32_t)z0 & 0xFFFFu) | ((uint32_t)z1 << 16);
+                zs[i] = valid ? z0 : 0;
+                zs[SA + i] = valid ? z1 : 0;
+                es[i] = valid ? (int32_t)(R - r2) : 0;
             }
             __syncwarp();
 
-            // eq. (6): G[k] = sum_i e_p[i] z_S2[i] x_S1[t0 + i - k], taps k = 8g + kk
+            // eq. (6): G[k] = sum_i e[i] z_S2[i] x_S1[t0 + i - k] for k = k0 .. k0 + 3
             if (mu < 63) {
-                int64_t acc[8];
+                int32_t xr[SA + 3];
+                const uint32_t *xb = xs + bb * SA + K - k0 - 3;
 #pragma unroll
-                for (int kk = 0; kk < 8; ++kk) acc[kk] = 0;
-                const uint32_t *xb = xs + bb * SA + K - 8 * g;
-#pragma unroll 4
+                for (int m = 0; m < SA + 3; ++m) xr[m] = sx8(xb[m], 8 * s1);
+                int64_t acc[4] = {0, 0, 0, 0};
+                const int32_t *zrow = zs + o * SA;
+#pragma unroll
                 for (int i = 0; i < SA; ++i) {
-                    const int32_t e = es[p * SA + i];
-                    const int32_t z = zs[s2 * SA + i];
+                    const int32_t e = es[i];
+                    const int32_t z = zrow[i];
 #pragma unroll
-                    for (int kk = 0; kk < 8; ++kk) {
-                        const int32_t xv = sx8(xb[i - kk], 8 * s1);
-                        acc[kk] += (int64_t)e * (int64_t)(z * xv);
-                    }
+                    for (int kk = 0; kk < 4; ++kk) acc[kk] += (int64_t)e * (int64_t)(z * xr[i - kk + 3]);
                 }
+                int32_t nv[4];
 #pragma unroll
-                for (int kk = 0; kk < 8; ++kk) {
-                    const int32_t mine = g ? T[8 + kk] : T[kk];
-                    int64_t v = (int64_t)mine + (acc[kk] >> mu);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int32_t cur = h ? (g ? T[12 + kk] : T[4 + kk]) : (g ? T[8 + kk] : T[kk]);
+                    int64_t v = (int64_t)cur + (acc[kk] >> mu);
                     v = v < -(1ll << 29) ? -(1ll << 29) : (v > (1ll << 29) - 1 ? (1ll << 29) - 1 : v);
-                    const int32_t nv = (int32_t)v;
-                    const int32_t other = __shfl_xor_sync(0xffffffffu, nv, 1);
-                    T[kk] = g ? other : nv;
-                    T[8 + kk] = g ? nv : other;
+                    nv[kk] = (int32_t)v;
+                }
+                // gather the filter's 16 taps from its four lanes (lane bit 0 = h, bit 1 = g)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int32_t a = nv[kk];                                 // (g, h)
+                    const int32_t b = __shfl_xor_sync(0xffffffffu, a, 1);     // (g, 1-h)
+                    const int32_t c2 = __shfl_xor_sync(0xffffffffu, a, 2);    // (1-g, h)
+                    const int32_t d = __shfl_xor_sync(0xffffffffu, b, 2);     // (1-g, 1-h)
+                    const int32_t q00 = g ? (h ? d : c2) : (h ? b : a);       // g=0, h=0
+                    const int32_t q01 = g ? (h ? c2 : d) : (h ? a : b);       // g=0, h=1
+                    const int32_t q10 = g ? (h ? b : a) : (h ? d : c2);       // g=1, h=0
+                    const int32_t q11 = g ? (h ? a : b) : (h ? c2 : d);       // g=1, h=1
+                    T[kk] = q00;
+                    T[4 + kk] = q01;
+                    T[8 + kk] = q10;
+                    T[12 + kk] = q11;
                 }
             }
         }
-        if (ch.write_state && g == 0) {
+        if (ch.write_state && g == 0 && h == 0) {
 #pragma unroll
             for (int k = 0; k < K; ++k) fr.state[(s2 * 4 + s1) * K + k] = T[k];
         }
@@ -188,7 +252,7 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
 }  // namespace
 
 size_t aeq_smem_bytes(int na, int warps) {
-    return (size_t)warps * (na == 64 ? AeqCfg<64>::WORDS : AeqCfg<32>::WORDS) * sizeof(uint32_t);
+    return (size_t)warps * (na == 64 ? AeqCfg<64, 4080>::WORDS : AeqCfg<32, 2>::WORDS) * sizeof(uint32_t);
 }
 
 cudaError_t aeq_configure() {
@@ -199,15 +263,18 @@ cudaError_t aeq_configure() {
                                 (int)aeq_smem_bytes(32, 4));
 }
 
+// Work items are (chain, polarisation) pairs: 2 per chain.
 cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,
                        int warps, int grid, cudaStream_t stream) {
     if (n_chains <= 0) return cudaSuccess;
     const dim3 block(32 * warps);
     const size_t smem = aeq_smem_bytes(na, warps);
+    const int n_items = 2 * n_chains;
+    if (grid <= 0) grid = (n_items + warps - 1) / warps;
     if (na == 64)
-        aeq_kernel<64, 4080><<<grid, block, smem, stream>>>(frames, chains, n_chains, prm);
+        aeq_kernel<64, 4080><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
     else
-        aeq_kernel<32, 2><<<grid, block, smem, stream>>>(frames, chains, n_chains, prm);
+        aeq_kernel<32, 2><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
     return cudaGetLastError();
 }
 

@@ -344,9 +344,9 @@ int work_kernel_count(const Work &w) {
     return k;
 }
 
-fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream) {
+fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream, int stages) {
     const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
-    if (w.op != FNT_OP_AEQ && !w.items.empty()) {
+    if ((stages & 1) && w.op != FNT_OP_AEQ && !w.items.empty()) {
         const int nw = p->cdc_warps;
         const int n = (int)w.items.size();
         const int grid = std::min((n + nw - 1) / nw, p->n_sm * 64);
@@ -354,12 +354,11 @@ fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaSt
                                    stream);
         if (e != cudaSuccess) return cuda_fail(e, "cdc kernel launch");
     }
-    if (w.op != FNT_OP_CDC && !w.chains.empty()) {
+    if ((stages & 2) && w.op != FNT_OP_CDC && !w.chains.empty()) {
         const int nw = p->aeq_warps;
         const int n = (int)w.chains.size();
-        const int grid = (n + nw - 1) / nw;
         AeqParams prm{p->d.mu_shift, p->d.rde_a};
-        cudaError_t e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(dev + w.off_chains), n, prm, nw, grid,
+        cudaError_t e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(dev + w.off_chains), n, prm, nw, 0,
                                    stream);
         if (e != cudaSuccess) return cuda_fail(e, "aeq kernel launch");
     }
@@ -517,6 +516,12 @@ extern "C" fnt_status fnt_batch_launch(fnt_batch *bt, void *stream_) {
     cudaError_t e = cudaGraphLaunch(bt->exec, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     return FNT_OK;
+}
+
+extern "C" fnt_status fnt_batch_launch_stage(fnt_batch *bt, int32_t stage, void *stream) {
+    if (!bt) return fail(FNT_ERR_INVALID, "null batch");
+    if (stage != 0 && stage != 1) return fail(FNT_ERR_INVALID, "stage must be 0 (CDC) or 1 (AEQ)");
+    return launch_work(bt->plan, bt->work, bt->dev, (cudaStream_t)stream, 1 << stage);
 }
 
 extern "C" int32_t fnt_batch_kernel_count(const fnt_batch *bt) { return bt ? work_kernel_count(bt->work) : 0; }

@@ -37,13 +37,13 @@ __device__ __forceinline__ int32_t sx8(uint32_t w, int sh) { return (int32_t)(w 
 
 __device__ __forceinline__ int32_t sat5(int32_t v) { return v < -16 ? -16 : (v > 15 ? 15 : v); }
 
-// One block of one polarisation: window words w[j] = win[j][lane]; result
-// packed (re | im << 16) into o[j][lane] for all 64 window positions.
-// `o` may be `win` itself: every output depends on every input of the lane's
-// column, so all reads precede all writes.
-__device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, const int32_t *hs, int lane,
-                                          int sh) {
-    int32_t P[kN];
+// One block of one polarisation: window words w[j] = win[j][lane]; results
+// (re, im) as int16 into o[j][lane] for all 64 window positions.  `o` may be
+// `win` itself: every output depends on every input of the lane's column, so
+// all reads precede all writes.  The two inverse transforms run as a two-trip
+// loop so that their unrolled code exists once (instruction-cache footprint).
+__device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, const int32_t *hs, int lane, int sh) {
+    int32_t P[kN], Q[kN];
 #pragma unroll
     for (int j = 0; j < kN; ++j) {
         const uint32_t w = win[j * kRow + lane];
@@ -52,8 +52,6 @@ __device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, cons
     fnt_fwd<kN, kAlpha>(P);
 #pragma unroll
     for (int i = 0; i < kN; ++i) P[i] = rho(rhoc(P[i]) * hs[i]);
-
-    int32_t Q[kN];
 #pragma unroll
     for (int j = 0; j < kN; ++j) {
         const uint32_t w = win[j * kRow + lane];
@@ -61,21 +59,25 @@ __device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, cons
     }
     fnt_fwd<kN, kAlpha>(Q);
 #pragma unroll
+    for (int i = 0; i < kN; ++i) Q[i] = rho(rhoc(Q[i]) * hs[kN + i]);
+#pragma unroll
     for (int i = 0; i < kN; ++i) {
-        const int32_t q = rho(rhoc(Q[i]) * hs[kN + i]);
-        const int32_t a = P[i] + q;
-        const int32_t b = P[i] - q;
-        P[i] = rho(a);
-        Q[i] = rho(b * -256);
+        const int32_t a = P[i] + Q[i];
+        const int32_t b = P[i] - Q[i];
+        P[i] = rho(a);              // eq. (7) spectrum (2^-1 N^-1 folded into H)
+        Q[i] = rho(b * -256);       // eq. (8) spectrum: 2^-9 = 2^-1 * (-2^8)
     }
-    fnt_inv<kN, kAlpha>(P);
+    int16_t *o16 = (int16_t *)o;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        fnt_inv<kN, kAlpha>(P);
+        // |z| <= 31 * 1024 < 32767, so the centred residue is the value
 #pragma unroll
-    for (int j = 0; j < kN; ++j) P[j] = decode(P[j]);
-    fnt_inv<kN, kAlpha>(Q);
+        for (int j = 0; j < kN; ++j) o16[2 * (j * kRow + lane) + pass] = (int16_t)rhoc(P[j]);
+        if (pass == 0) {
 #pragma unroll
-    for (int j = 0; j < kN; ++j) {
-        const int32_t im = decode(Q[j]);
-        o[j * kRow + lane] = ((uint32_t)P[j] & 0xFFFFu) | ((uint32_t)im << 16);
+            for (int i = 0; i < kN; ++i) P[i] = Q[i];
+        }
     }
 }
 
@@ -123,6 +125,7 @@ __global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict_
         // Input windows: window l covers samples base + l*S + [0, 64).
         const int64_t base = b0 * S - (kN - S);
         const int esz = 2 * npol;
+#pragma unroll 8
         for (int l = 0; l < 32; ++l) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -138,10 +141,10 @@ __global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict_
         }
         __syncwarp();
 
-        cdc_block(win, o0, hs, lane, 0);
-        if (npol == 2) {
-            __syncwarp();
-            cdc_block(win, win, hs, lane, 16);   // each lane reads and writes only its own column
+#pragma unroll 1
+        for (int pol = 0; pol < npol; ++pol) {
+            // pol 0 results go to o0; pol 1 results overwrite the lane's own window column
+            cdc_block(win, pol ? win : o0, hs, lane, 16 * pol);
         }
         __syncwarp();
 

@@ -42,7 +42,8 @@ struct Work {
 fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work &w);
 void layout(Work &w);
 fnt_status upload_work(Work &w, char *dev, cudaStream_t stream);
-fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream);
+// stages: bit 0 = CDC kernel, bit 1 = AEQ kernel
+fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream, int stages = 3);
 int work_kernel_count(const Work &w);
 
 // kernels

@@ -1,0 +1,201 @@
+"""Serving session on the GPU: continuous batching over links with device-
+resident AEQ state, checked bit-exactly against the oracle's sequential
+per-link processing, alone and in the mix; admission cap, checkpoint/resume,
+host-side fault injection."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2405_04253_gb300 as F  # noqa: E402
+
+MU = 9
+
+
+def make_links(rng, n_links):
+    return [rng.integers(-32, 32, (int(rng.choice([5, 9, 17, 19])), 2)).astype(np.int8) for _ in range(n_links)]
+
+
+def make_frames(rng, n_links, per_link, lo=200, hi=5000):
+    frames = []
+    for i in range(n_links * per_link):
+        link = int(rng.integers(0, n_links))
+        n = int(rng.integers(lo, hi))
+        frames.append((link, rng.integers(-16, 16, (n, 2, 2)).astype(np.int8)))
+    return frames
+
+
+def oracle_sequential(orc, links, frames):
+    prm = orc.ChainParams(mu_shift=MU)
+    T = {l: orc.aeq_init_taps(16, prm.w0) for l in range(len(links))}
+    outs = []
+    for link, x in frames:
+        out, T[link] = orc.chain(x, links[link], prm, T0=T[link])
+        outs.append(out)
+    return outs, T
+
+
+def run_session(plan, links, frames, cap=1 << 30, streams=4, one_at_a_time=False, host=False):
+    s = F.Session(plan, len(links), cap, streams)
+    for l, taps in enumerate(links):
+        s.set_link(l, taps)
+    outs = [None] * len(frames)
+    tickets = {}
+    done = 0
+    for i, (link, x) in enumerate(frames):
+        nsym = F.chain_nsym(x.shape[0], links[link].shape[0])
+        if host:
+            xd = torch.from_numpy(x).pin_memory()
+            od = torch.zeros((nsym, 4), dtype=torch.int16).pin_memory()
+        else:
+            xd = torch.from_numpy(x).cuda()
+            od = torch.zeros((nsym, 4), dtype=torch.int16, device="cuda")
+        torch.cuda.synchronize()
+        while True:
+            tk = s.try_submit(link, xd, od)
+            if tk is not None:
+                break
+            for c in s.poll(timeout_us=100000):
+                assert c["status"] == F.FNT_OK
+                done += 1
+        tickets[tk] = (i, od)
+        if one_at_a_time:
+            while s.pending():
+                for c in s.poll(timeout_us=100000):
+                    assert c["status"] == F.FNT_OK
+                    done += 1
+    while s.pending():
+        for c in s.poll(timeout_us=100000):
+            assert c["status"] == F.FNT_OK
+            done += 1
+    assert done == len(frames)
+    for tk, (i, od) in tickets.items():
+        outs[i] = od.cpu().numpy()
+    states = [s.get_link_state(l) for l in range(len(links))]
+    s.close()
+    return outs, states
+
+
+def test_session_mix_matches_sequential_oracle_and_alone(orc):
+    rng = np.random.default_rng(21)
+    links = make_links(rng, 6)
+    frames = make_frames(rng, 6, 4)
+    plan = F.Plan(mu_shift=MU)
+    ref, Tref = oracle_sequential(orc, links, frames)
+    mix, Tmix = run_session(plan, links, frames)
+    alone, Talone = run_session(plan, links, frames, one_at_a_time=True, streams=1)
+    for i in range(len(frames)):
+        assert np.array_equal(mix[i], ref[i]), i
+        assert np.array_equal(alone[i], mix[i]), i
+    for l in range(len(links)):
+        assert np.array_equal(Tmix[l], Tref[l])
+        assert np.array_equal(Talone[l], Tref[l])
+
+
+def test_session_host_pinned_buffers(orc):
+    rng = np.random.default_rng(22)
+    links = make_links(rng, 3)
+    frames = make_frames(rng, 3, 3)
+    ref, _ = oracle_sequential(orc, links, frames)
+    got, _ = run_session(F.Plan(mu_shift=MU), links, frames, host=True)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+def test_session_admission_cap_refuses_then_admits():
+    rng = np.random.default_rng(23)
+    links = make_links(rng, 2)
+    plan = F.Plan(mu_shift=MU)
+    s = F.Session(plan, 2, 64 * 1024, 1)
+    for l, t in enumerate(links):
+        s.set_link(l, t)
+    x = torch.from_numpy(rng.integers(-16, 16, (20000, 2, 2)).astype(np.int8)).cuda()
+    o1 = torch.zeros((F.chain_nsym(20000, links[0].shape[0]), 4), dtype=torch.int16, device="cuda")
+    o2 = torch.zeros((F.chain_nsym(20000, links[1].shape[0]), 4), dtype=torch.int16, device="cuda")
+    t1 = s.submit(0, x, o1)             # 10000 symbols x 4 B = 40 KB of the 64 KB cap
+    assert s.try_submit(1, x, o2) is None
+    got = []
+    while not got:
+        got = s.poll(timeout_us=1000000)
+    assert got[0]["ticket"] == t1 and got[0]["status"] == F.FNT_OK
+    assert s.try_submit(1, x, o2) is not None
+    s.close()
+    with pytest.raises(F.FntError) as e:
+        s2 = F.Session(plan, 1, 64 * 1024, 1)
+        s2.set_link(0, links[0])
+        big = torch.zeros((200000, 2, 2), dtype=torch.int8, device="cuda")
+        ob = torch.zeros((100000, 4), dtype=torch.int16, device="cuda")
+        s2.submit(0, big, ob)
+    assert e.value.status == F.FNT_ERR_BOUND
+
+
+def test_session_checkpoint_resume_bit_exact(orc):
+    rng = np.random.default_rng(24)
+    links = make_links(rng, 2)
+    frames = make_frames(rng, 2, 4)
+    plan = F.Plan(mu_shift=MU)
+    full, Tfull = run_session(plan, links, frames)
+    k = len(frames) // 2
+    first, Tmid = run_session(plan, links, frames[:k])
+    s = F.Session(plan, len(links), 1 << 30, 2)
+    for l, taps in enumerate(links):
+        s.set_link(l, taps)
+        s.set_link_state(l, Tmid[l])
+    outs = []
+    for link, x in frames[k:]:
+        od = torch.zeros((F.chain_nsym(x.shape[0], links[link].shape[0]), 4), dtype=torch.int16, device="cuda")
+        s.submit(link, torch.from_numpy(x).cuda(), od)
+        outs.append(od)
+    while s.pending():
+        for c in s.poll(timeout_us=100000):
+            assert c["status"] == F.FNT_OK
+    for i, od in enumerate(outs):
+        assert np.array_equal(od.cpu().numpy(), full[k + i])
+    for l in range(len(links)):
+        assert np.array_equal(s.get_link_state(l), Tfull[l])
+    s.close()
+
+
+def test_session_injected_failure_recovers(orc):
+    rng = np.random.default_rng(25)
+    links = make_links(rng, 1)
+    plan = F.Plan(mu_shift=MU)
+    s = F.Session(plan, 1, 1 << 28, 1)
+    s.set_link(0, links[0])
+    x = rng.integers(-16, 16, (3000, 2, 2)).astype(np.int8)
+    xd = torch.from_numpy(x).cuda()
+    od = torch.zeros((F.chain_nsym(3000, links[0].shape[0]), 4), dtype=torch.int16, device="cuda")
+    T0 = s.get_link_state(0)
+    s.inject_failures(1)
+    s.submit(0, xd, od)
+    res = []
+    while not res:
+        res = s.poll(timeout_us=1000000)
+    assert res[0]["status"] == F.FNT_ERR_CUDA
+    assert np.array_equal(s.get_link_state(0), T0)          # state untouched
+    s.submit(0, xd, od)
+    res = []
+    while not res:
+        res = s.poll(timeout_us=1000000)
+    assert res[0]["status"] == F.FNT_OK
+    ref, _ = orc.chain(x, links[0], orc.ChainParams(mu_shift=MU))
+    assert np.array_equal(od.cpu().numpy(), ref)
+    assert s.poll(timeout_us=1000) == []                     # nothing pending: times out
+    s.close()
+
+
+def test_session_rejects_pageable_host_buffers():
+    plan = F.Plan()
+    s = F.Session(plan, 1, 1 << 20, 1)
+    s.set_link(0, np.ones((5, 2), np.int8))
+    x = np.zeros((100, 2, 2), np.int8)
+    o = np.zeros((50, 4), np.int16)
+    with pytest.raises(F.FntError) as e:
+        s.submit(0, x, o)
+    assert e.value.status == F.FNT_ERR_INVALID
+    s.close()

@@ -1,0 +1,134 @@
+"""CPU-only checks of the boundary and host logic: the C-ABI library builds,
+loads and exports every symbol include/fnt.h declares (no compute calls), the
+binding covers them, and the multi-rank timing reduction of bench.py works
+across world_size-2 gloo ranks."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            with open(os.path.join(ROOT, "include", fn)) as fh:
+                names += re.findall(r"FNT_API[^;(]*?\b(fnt_\w+)\s*\(", fh.read())
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libfnt():
+    import paper_2405_04253_gb300 as fnt
+    path = fnt.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for must in ("fnt_plan_create", "fnt_cdc_run", "fnt_aeq_run", "fnt_cdc_aeq_run", "fnt_session_submit",
+                 "fnt_session_poll"):
+        assert must in names
+    assert len(names) >= 20
+
+
+def test_library_exports_every_declared_symbol(libfnt):
+    missing = [n for n in header_functions() if not hasattr(libfnt, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_2405_04253_gb300 as fnt
+    assert sorted(fnt.SIGNATURES) == header_functions()
+
+
+def test_library_is_sm103a_only():
+    import importlib
+    b = importlib.import_module("paper_2405_04253_gb300.build")
+    assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_version_and_defaults_without_gpu(libfnt):
+    import paper_2405_04253_gb300 as fnt
+    lib = fnt.lib()
+    assert lib.fnt_version().decode().startswith("fnt ")
+    d = fnt.default_desc()
+    assert (d.n_cdc, d.alpha_cdc, d.n_aeq, d.alpha_aeq, d.aeq_taps) == (64, 4080, 32, 2, 16)
+
+
+def test_plan_rejects_invalid_radix_without_gpu():
+    # eq. (4) is checked on the host before any device call
+    import paper_2405_04253_gb300 as fnt
+    with pytest.raises(fnt.FntError) as e:
+        fnt.Plan(alpha_cdc=2)
+    assert e.value.status == fnt.FNT_ERR_BOUND
+    with pytest.raises(fnt.FntError) as e:
+        fnt.Plan(n_aeq=32, alpha_aeq=4)            # order 16: alpha^32 = 1 but order != 32
+    assert e.value.status == fnt.FNT_ERR_BOUND
+
+
+def test_product_package_does_not_import_oracle():
+    for dirpath, _, files in os.walk(os.path.join(ROOT, "paper_2405_04253_gb300")):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                with open(os.path.join(dirpath, f)) as fh:
+                    txt = fh.read()
+                assert "import oracle" not in txt and "fnt_oracle" not in txt, f
+
+
+def test_oracle_does_not_import_product():
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            with open(os.path.join(ROOT, "oracle", f)) as fh:
+                txt = fh.read()
+            assert "paper_2405_04253_gb300" not in txt and "fnt.h" not in txt
+
+
+def test_bench_op_model():
+    import bench
+    assert bench.butterflies(64) == 192 and bench.butterflies(32) == 80
+    # 2 pols x 2 fwd + 2 inv transforms x 192 butterflies x 6 + 2 x 64 products x 3, per 48-sample block
+    assert bench.cdc_ops(48, 48) == 2 * (4 * 192 * 6 + 128 * 3)
+    assert bench.aeq_ops(48, 64) == 68 * 192 * 6 + 32 * 64 * 3 + 16 * 16 * 48 * 2
+    assert bench.alu_peak_ops() == pytest.approx(40.27e12, rel=1e-3)
+
+
+def _gloo_worker(rank, world, port, q):
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world, init_method=f"tcp://127.0.0.1:{port}")
+    ms = [3.0, 5.0][rank]
+    m = bench.reduce_max(ms)
+    q.put((rank, m, bench.aggregate(1000, world, m * 1e-3)))
+    dist.destroy_process_group()
+
+
+def test_multirank_timing_reduction_gloo():
+    import multiprocessing as mp
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_gloo_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, m, v in res:
+        assert m == 5.0                                 # slowest rank's time
+        assert v == pytest.approx(2 * 1000 / 5e-3 / 1e9)
+
+
+def test_single_rank_reduce_is_identity():
+    import bench
+    assert bench.reduce_max(1.25) == 1.25
+    assert bench.aggregate(2 ** 21, 1, 1e-3) == pytest.approx(2 ** 21 / 1e-3 / 1e9)
