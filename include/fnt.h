@@ -220,6 +220,33 @@ FNT_API fnt_status fnt_batch_destroy(fnt_batch *b);
  * launches of this plan (autotuner hook).  0 keeps the current value. */
 FNT_API fnt_status fnt_plan_set_launch(fnt_plan *plan, int32_t cdc_warps, int32_t aeq_warps);
 
+/* ------------------------------------------------- allocation-free chain ---- */
+
+/* Largest frame (samples) and AEQ segment count fnt_cdc_aeq_run_noalloc takes. */
+#define FNT_NOALLOC_MAX_SAMPLES (1 << 21)
+#define FNT_NOALLOC_MAX_SEGMENTS 4096
+
+/*
+ * The receiver chain of fnt_cdc_aeq_run for ONE frame, without allocating any
+ * memory.  The paper has no counterpart: this exists for callers that cannot
+ * allocate device memory where they process a frame (a latency-critical receive
+ * loop that cannot afford an allocation's synchronisation or latency, or an
+ * application that owns all device memory through its own allocator).
+ *
+ * The caller passes the frame as for fnt_cdc_aeq_run (device in / out / state,
+ * host taps).  The work tables and the intermediate CDC -> AEQ symbols live in
+ * a fixed array of about 4.2 MiB in device memory that belongs to the library
+ * image: every GPU that loads libfnt holds it until the process exits.  The
+ * first call on a device, with that device current, looks up the array's
+ * address; make that first call before any stream capture.  All calls on a
+ * device share the array and overwrite it, so calls whose work overlaps on the
+ * GPU race: keep them on one stream or wait between them.  Frames longer than
+ * FNT_NOALLOC_MAX_SAMPLES, or plans that cut one into more than
+ * FNT_NOALLOC_MAX_SEGMENTS AEQ segments, are rejected with FNT_ERR_BOUND before
+ * anything is enqueued.  Results equal fnt_cdc_aeq_run's bit for bit.
+ */
+FNT_API fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *plan, const fnt_frame *frame, void *stream);
+
 /* ---------------------------------------------------------------- serving ---- */
 
 /*

@@ -69,6 +69,7 @@ SIGNATURES = {
     "fnt_batch_launch_stage": (_I32, [_VP, _I32, _VP]),
     "fnt_batch_kernel_count": (_I32, [_VP]),
     "fnt_batch_destroy": (_I32, [_VP]),
+    "fnt_cdc_aeq_run_noalloc": (_I32, [_VP, ctypes.POINTER(FrameC), _VP]),
     "fnt_session_create": (_I32, [_VP, _I32, _SZ, _I32, ctypes.POINTER(_VP)]),
     "fnt_session_set_link": (_I32, [_VP, _I32, _VP, _I32]),
     "fnt_session_submit": (_I32, [_VP, _I32, _VP, _I64, _VP, ctypes.POINTER(ctypes.c_uint64)]),
@@ -192,6 +193,17 @@ def cdc_aeq_run(plan: Plan, frames, stream=None, host: bool = False):
     b, keep = _batch(frames, host)
     check(lib().fnt_cdc_aeq_run(plan.handle, ctypes.byref(b),
                                 None if host and stream is None else _stream_handle(stream)))
+
+
+NOALLOC_MAX_SAMPLES = 1 << 21
+
+
+def cdc_aeq_run_noalloc(plan: Plan, frame: Frame, stream=None):
+    """The chain for one frame through fnt_cdc_aeq_run_noalloc: no memory is
+    allocated; its scratch is a fixed device array inside libfnt shared by all
+    calls on the device (see include/fnt.h)."""
+    fc = frame.c()
+    check(lib().fnt_cdc_aeq_run_noalloc(plan.handle, ctypes.byref(fc), _stream_handle(stream)))
 
 
 class Batch:

@@ -1,0 +1,71 @@
+"""fnt_cdc_aeq_run_noalloc: the one-frame chain for callers that cannot allocate
+device memory where they process a frame (a latency-critical receive loop, or an
+application whose own allocator owns all device memory).  Its scratch is a fixed
+array inside libfnt; the results must equal those of fnt_cdc_aeq_run bit for
+bit, call after call.  This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2405_04253_gb300 as F  # noqa: E402
+import synth  # noqa: E402
+
+
+def _poison(nsym):
+    return torch.full((nsym, 4), 0x5A5A, dtype=torch.int16, device="cuda")
+
+
+def test_noalloc_equals_allocating_entry_point_twice_segmented():
+    f = synth.config2(1 << 15)
+    plan = F.Plan(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=2048, aeq_warmup=512)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    x = torch.from_numpy(f.x).cuda()
+    ref = _poison(nsym)
+    F.cdc_aeq_run(plan, [F.Frame(x, ref, f.taps)])
+    torch.cuda.synchronize()
+    for _ in range(2):
+        out = _poison(nsym)
+        F.cdc_aeq_run_noalloc(plan, F.Frame(x, out, f.taps))
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+
+
+def test_noalloc_equals_allocating_entry_point_twice_with_state():
+    rng = np.random.default_rng(31)
+    plan = F.Plan(mu_shift=9)
+    init = torch.zeros((4, 4, 16), dtype=torch.int32, device="cuda")
+    init[[0, 1, 2, 3], [0, 1, 2, 3], 8] = 2048 << 16
+    st_ref, st_new = init.clone(), init.clone()
+    for call in range(2):
+        n = int(rng.integers(3000, 9000))
+        L = int(rng.choice([5, 17, 19]))
+        xh = rng.integers(-16, 16, (n, 2, 2)).astype(np.int8)
+        taps = rng.integers(-32, 32, (L, 2)).astype(np.int8)
+        x = torch.from_numpy(xh).cuda()
+        nsym = F.chain_nsym(n, L)
+        ref, out = _poison(nsym), _poison(nsym)
+        F.cdc_aeq_run(plan, [F.Frame(x, ref, taps, st_ref)])
+        F.cdc_aeq_run_noalloc(plan, F.Frame(x, out, taps, st_new))
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), call
+        assert torch.equal(st_new, st_ref), call
+
+
+def test_noalloc_rejects_frames_beyond_its_scratch():
+    plan = F.Plan()
+    x = torch.zeros((8, 2, 2), dtype=torch.int8, device="cuda")
+    out = torch.zeros((8, 4), dtype=torch.int16, device="cuda")
+    taps = np.ones((17, 2), np.int8)
+    with pytest.raises(F.FntError) as e:
+        F.cdc_aeq_run_noalloc(plan, F.Frame(x, out, taps, n=F.NOALLOC_MAX_SAMPLES + 2))
+    assert e.value.status == F.FNT_ERR_BOUND
+    tiny = F.Plan(aeq_segment=16, aeq_warmup=0)
+    with pytest.raises(F.FntError) as e:
+        F.cdc_aeq_run_noalloc(tiny, F.Frame(x, out, taps, n=F.NOALLOC_MAX_SAMPLES))
+    assert e.value.status == F.FNT_ERR_BOUND
