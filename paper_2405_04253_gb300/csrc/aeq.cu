@@ -53,12 +53,13 @@ struct AeqCfg {
 
 __device__ __forceinline__ int32_t sx8(uint32_t w, int sh) { return (int32_t)(w << (24 - sh)) >> 24; }
 
-// Lane h = 1 of the forward split: (a_j - 0) * alpha^j for the zero-padded taps.
+// Lane h = 1 of the forward split: (a_j - 0) * alpha^j for the zero-padded taps
+// (|result| < 2^17).
 template <int NA, int64_t ALPHA, int J>
 struct SplitTaps {
     static __device__ __forceinline__ void run(int32_t (&x)[NA / 2], const int32_t (&w)[kAeqK], bool odd) {
         constexpr int32_t W = TwTab<NA, ALPHA>::tab.w[J];
-        x[J] = odd ? mulc<W>(w[J]) : w[J];
+        x[J] = odd ? rho(w[J] * W) : w[J];                          // |w W| < 2^22
         if constexpr (J + 1 < kAeqK) SplitTaps<NA, ALPHA, J + 1>::run(x, w, odd);
     }
 };
@@ -69,7 +70,7 @@ template <int NA, int64_t AINV, int J, int FROM>
 struct JoinHalves {
     static __device__ __forceinline__ void run(const int32_t (&x)[NA / 2], int32_t (&res)[NA / 2], bool odd) {
         constexpr int32_t W = TwTab<NA, AINV>::tab.w[J];
-        const int32_t t = odd ? mulc<W>(x[J]) : x[J];             // lane 1 sends alpha^-n' E1[n']
+        const int32_t t = odd ? mulb<18, W>(x[J]) : x[J];         // lane 1 sends alpha^-n' E1[n']
         const int32_t r = __shfl_xor_sync(0xffffffffu, t, 1);
         res[J] = rhoc(odd ? r - t : t + r);                       // |true value| <= 32512
         if constexpr (J + 1 < NA / 2) JoinHalves<NA, AINV, J + 1, FROM>::run(x, res, odd);
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                     int32_t x[NA];
 #pragma unroll
                     for (int j = 0; j < NA; ++j) x[j] = sx8(xs[bq * SA + j], 8 * sq);
-                    fnt_fwd<NA, ALPHA>(x);
+                    fnt_fwd<NA, ALPHA, 5>(x);                  // |x| <= 16
                     int32_t *row = xf + (bq * 4 + sq) * C::XF_ROW;
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh)
@@ -157,13 +158,13 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
 #pragma unroll
             for (int j = K; j < M; ++j) y[j] = 0;
             if constexpr (M >= 2 * K)
-                fnt_fwd_halfzero<M, C::ALPHA2>(y);
+                fnt_fwd_halfzero<M, C::ALPHA2, 17>(y);
             else
-                fnt_fwd<M, C::ALPHA2>(y);
+                fnt_fwd<M, C::ALPHA2, 17>(y);
             const int32_t *xrow = xf + (bb * 4 + s1) * C::XF_ROW + h * C::HALF;
 #pragma unroll
             for (int j = 0; j < M; ++j) y[j] = rho(rhoc(y[j]) * xrow[j]);
-            fnt_inv<M, C::ALPHA2>(y);
+            fnt_inv<M, C::ALPHA2, 17>(y);
             int32_t c[M];
             JoinHalves<NA, C::AINV, 0, 0>::run(y, c, odd);
             {

@@ -49,7 +49,7 @@ __device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, cons
         const uint32_t w = win[j * kRow + lane];
         P[j] = sx8(w, sh) + 256 * sx8(w, sh + 8);
     }
-    fnt_fwd<kN, kAlpha>(P);
+    fnt_fwd<kN, kAlpha, 13>(P);                      // |u| <= 16 + 256 * 16 < 2^13
 #pragma unroll
     for (int i = 0; i < kN; ++i) P[i] = rho(rhoc(P[i]) * hs[i]);
 #pragma unroll
@@ -57,7 +57,7 @@ __device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, cons
         const uint32_t w = win[j * kRow + lane];
         Q[j] = sx8(w, sh) - 256 * sx8(w, sh + 8);
     }
-    fnt_fwd<kN, kAlpha>(Q);
+    fnt_fwd<kN, kAlpha, 13>(Q);
 #pragma unroll
     for (int i = 0; i < kN; ++i) Q[i] = rho(rhoc(Q[i]) * hs[kN + i]);
 #pragma unroll
@@ -70,7 +70,7 @@ __device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, cons
     int16_t *o16 = (int16_t *)o;
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
-        fnt_inv<kN, kAlpha>(P);
+        fnt_inv<kN, kAlpha, 17>(P);
         // |z| <= 31 * 1024 < 32767, so the centred residue is the value
 #pragma unroll
         for (int j = 0; j < kN; ++j) o16[2 * (j * kRow + lane) + pass] = (int16_t)rhoc(P[j]);

@@ -96,36 +96,76 @@ FNT_HD int32_t decode(int32_t x) {
     return r;
 }
 
-// Multiply a lazy residue (|x| < 2^18) by a centred compile-time constant.
-template <int32_t W>
-FNT_HD int32_t mulc(int32_t x) {
-    if constexpr (W == 1) {
-        return rho(x);
-    } else if constexpr (W == -1) {
-        return rho(-x);
-    } else if constexpr (W <= 4096 && W >= -4096) {
-        return rho(x * W);               // |x W| < 2^30
-    } else {
-        return rho(rhoc(x) * W);         // |rhoc(x)| <= 2^15 + 4, |W| <= 2^15
-    }
-}
-
 // Runtime variant for a centred constant w (|w| <= 2^15) and |x| < 2^30.
 FNT_HD int32_t mulw(int32_t x, int32_t w) { return rho(rhoc(x) * w); }
 
 // -------------------------------------------------------------- transforms ----
+//
+// Lazy reduction.  Every register of a transform carries a compile-time bound
+// b (|x| < 2^b), computed stage by stage in a constexpr plan from the bound of
+// the inputs.  A butterfly reduces its sum only when the sum's bound would pass
+// LIM, keeps a twiddle product unreduced while it stays under LIM, multiplies
+// directly when |d| |w| < 2^31 and pre-reduces with rhoc only when it would
+// not.  With LIM = 21 most butterflies cost 4-5 integer instructions instead
+// of 8-10 for full reduction, and no intermediate ever leaves int32.
 
-// One DIF butterfly with twiddle index e of a length-N network of radix ALPHA.
-template <int N, int64_t ALPHA, int E>
-FNT_HD void bfly(int32_t &a, int32_t &b) {
-    constexpr int32_t W = TwTab<N, ALPHA>::tab.w[E];
-    const int32_t s = a + b;
-    const int32_t d = a - b;
-    a = rho(s);
-    b = mulc<W>(d);
+constexpr int bits_of(int64_t v) {   // smallest m with |v| <= 2^m
+    int64_t a = v < 0 ? -v : v;
+    int m = 0;
+    while (((int64_t)1 << m) < a) ++m;
+    return m;
 }
 
-template <int N, int64_t ALPHA, bool BR, int S, int J>
+constexpr int kLazyLim = 21;
+
+enum : unsigned char { kSumLazy = 0, kSumRho = 1 };
+enum : unsigned char { kDiffLazy = 0, kDiffRho = 1, kMulLazy = 2, kMulRho = 3, kMulRhoc = 4 };
+
+template <int N, int64_t ALPHA, int INB, int OUTB>
+struct LazyPlan {
+    static constexpr int LOGN = ilog2(N);
+    int b[LOGN + 1][N];                 // bound of position i at the input of stage s
+    unsigned char ms[LOGN][N / 2];      // sum branch
+    unsigned char md[LOGN][N / 2];      // difference branch
+    constexpr LazyPlan() : b(), ms(), md() {
+        for (int i = 0; i < N; ++i) b[0][i] = INB;
+        for (int s = 0; s < LOGN; ++s) {
+            const int half = N >> (s + 1);
+            const int lim = (s + 1 == LOGN) ? (OUTB < kLazyLim ? OUTB : kLazyLim) : kLazyLim;
+            for (int j = 0; j < N / 2; ++j) {
+                const int blk = j / half, jj = j % half;
+                const int i0 = blk * 2 * half + jj, i1 = i0 + half;
+                const int bsum = (b[s][i0] > b[s][i1] ? b[s][i0] : b[s][i1]) + 1;
+                if (bsum > lim) {
+                    ms[s][j] = kSumRho;
+                    b[s + 1][i0] = 17;
+                } else {
+                    ms[s][j] = kSumLazy;
+                    b[s + 1][i0] = bsum;
+                }
+                const int64_t w = zcent(zpow(ALPHA, (int64_t)jj << s));
+                if (w == 1) {
+                    md[s][j] = bsum > lim ? kDiffRho : kDiffLazy;
+                    b[s + 1][i1] = bsum > lim ? 17 : bsum;
+                } else if (bsum + bits_of(w) <= 30) {
+                    const int pb = bsum + bits_of(w);
+                    md[s][j] = pb > lim ? kMulRho : kMulLazy;
+                    b[s + 1][i1] = pb > lim ? 17 : pb;
+                } else {
+                    md[s][j] = kMulRhoc;
+                    b[s + 1][i1] = 17;
+                }
+            }
+        }
+    }
+};
+
+template <int N, int64_t ALPHA, int INB, int OUTB>
+struct LazyTab {
+    static constexpr LazyPlan<N, ALPHA, INB, OUTB> plan{};
+};
+
+template <int N, int64_t ALPHA, int INB, int OUTB, bool BR, int S, int J>
 struct DifStage {
     static FNT_HD void run(int32_t (&x)[N]) {
         constexpr int LOGN = ilog2(N);
@@ -136,48 +176,77 @@ struct DifStage {
         constexpr int I1 = I0 + HALF;
         constexpr int R0 = BR ? bitrev(I0, LOGN) : I0;
         constexpr int R1 = BR ? bitrev(I1, LOGN) : I1;
-        bfly<N, ALPHA, (JJ << S)>(x[R0], x[R1]);
-        if constexpr (J + 1 < N / 2) DifStage<N, ALPHA, BR, S, J + 1>::run(x);
+        constexpr int32_t W = TwTab<N, ALPHA>::tab.w[JJ << S];
+        constexpr unsigned char MS = LazyTab<N, ALPHA, INB, OUTB>::plan.ms[S][J];
+        constexpr unsigned char MD = LazyTab<N, ALPHA, INB, OUTB>::plan.md[S][J];
+        const int32_t a = x[R0], b = x[R1];
+        const int32_t s = a + b;
+        const int32_t d = a - b;
+        x[R0] = MS == kSumRho ? rho(s) : s;
+        if constexpr (MD == kDiffLazy) {
+            x[R1] = d;
+        } else if constexpr (MD == kDiffRho) {
+            x[R1] = rho(d);
+        } else if constexpr (MD == kMulLazy) {
+            x[R1] = d * W;
+        } else if constexpr (MD == kMulRho) {
+            x[R1] = rho(d * W);
+        } else {
+            x[R1] = rho(rhoc(d) * W);
+        }
+        if constexpr (J + 1 < N / 2) DifStage<N, ALPHA, INB, OUTB, BR, S, J + 1>::run(x);
     }
 };
 
-template <int N, int64_t ALPHA, bool BR, int S>
+template <int N, int64_t ALPHA, int INB, int OUTB, bool BR, int S>
 struct Dif {
     static FNT_HD void run(int32_t (&x)[N]) {
-        DifStage<N, ALPHA, BR, S, 0>::run(x);
-        if constexpr (S + 1 < ilog2(N)) Dif<N, ALPHA, BR, S + 1>::run(x);
+        DifStage<N, ALPHA, INB, OUTB, BR, S, 0>::run(x);
+        if constexpr (S + 1 < ilog2(N)) Dif<N, ALPHA, INB, OUTB, BR, S + 1>::run(x);
     }
 };
 
-// Forward transform, eq. (1) without the final reduction: natural order in
-// (|x| < 2^17), X[k] in register bitrev(k) out (|X| < 2^17).
-template <int N, int64_t ALPHA>
+// Forward transform, eq. (1) up to the final reduction: natural order in with
+// |x| < 2^INB, X[k] in register bitrev(k) out with |X| < 2^18.
+template <int N, int64_t ALPHA, int INB = 17, int OUTB = 18>
 FNT_HD void fnt_fwd(int32_t (&x)[N]) {
-    Dif<N, ALPHA, false, 0>::run(x);
+    Dif<N, ALPHA, INB, OUTB, false, 0>::run(x);
 }
 
 // Inverse transform, eq. (2) without the factor N^-1: P[k] in register
-// bitrev(k) in, p[n] in register n out.
-template <int N, int64_t ALPHA>
+// bitrev(k) in, p[n] in register n out; bounds as for fnt_fwd.
+template <int N, int64_t ALPHA, int INB = 17, int OUTB = 18>
 FNT_HD void fnt_inv(int32_t (&x)[N]) {
-    Dif<N, zinv(ALPHA), true, 0>::run(x);
+    Dif<N, zinv(ALPHA), INB, OUTB, true, 0>::run(x);
 }
 
-// Forward transform of a sequence whose entries NZ..N-1 are zero (NZ <= N/2):
-// the first stage reduces to (a, a * w).
-template <int N, int64_t ALPHA, int J>
+// Multiply a lazy value with |x| < 2^XB by a centred constant W, reduced.
+template <int XB, int32_t W>
+FNT_HD int32_t mulb(int32_t x) {
+    if constexpr (W == 1) {
+        return rho(x);
+    } else if constexpr (XB + bits_of(W) <= 30) {
+        return rho(x * W);
+    } else {
+        return rho(rhoc(x) * W);
+    }
+}
+
+// Forward transform of a sequence whose entries N/2..N-1 are zero: the first
+// stage reduces to (a, a * w); inputs |x| < 2^INB.
+template <int N, int64_t ALPHA, int INB, int J>
 struct DifFirstZeroPad {
     static FNT_HD void run(int32_t (&x)[N]) {
         constexpr int32_t W = TwTab<N, ALPHA>::tab.w[J];
-        x[J + N / 2] = mulc<W>(x[J]);
-        if constexpr (J + 1 < N / 2) DifFirstZeroPad<N, ALPHA, J + 1>::run(x);
+        x[J + N / 2] = mulb<INB, W>(x[J]);
+        if constexpr (J + 1 < N / 2) DifFirstZeroPad<N, ALPHA, INB, J + 1>::run(x);
     }
 };
 
-template <int N, int64_t ALPHA>
+template <int N, int64_t ALPHA, int INB = 17, int OUTB = 18>
 FNT_HD void fnt_fwd_halfzero(int32_t (&x)[N]) {
-    DifFirstZeroPad<N, ALPHA, 0>::run(x);
-    if constexpr (N > 2) Dif<N, ALPHA, false, 1>::run(x);
+    DifFirstZeroPad<N, ALPHA, INB, 0>::run(x);
+    if constexpr (N > 2) Dif<N, ALPHA, (INB > 17 ? INB : 17), OUTB, false, 1>::run(x);
 }
 
 }  // namespace fnt
