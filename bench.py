@@ -6,7 +6,8 @@ requantise + resample, FNT-AEQ with RDE adaptation) over one batch of synthetic
 input already resident in device memory.  Default workload: one PDM-16QAM
 stream, 40 GBaud at 2 samples/symbol, 2^20 symbols per polarisation, 75 km
 (17 CD taps, 6 bit), 5-bit I/Q, AEQ 4x4 RV-MIMO at N = 64 / radix 4080 in
-segments of 2048 symbols with 512 warm-up symbols.
+segments of 1024 symbols with 128 warm-up symbols, every segment starting from
+the tap state the previous step ended with (a stream processed step by step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fnt|reference]
 
@@ -40,15 +41,16 @@ UNIT = "Gsamples/s"
 # ---------------------------------------------------------------- workload ----
 
 WORKLOADS = {
-    "cfg2": dict(n_sym=1 << 20, km=75.0, n_aeq=64, alpha_aeq=4080, segment=2048, warmup=512,
+    "cfg2": dict(n_sym=1 << 20, km=75.0, n_aeq=64, alpha_aeq=4080, segment=1024, warmup=128,
                  desc="PDM-16QAM 40 GBaud 2 sps, 2^20 symbols/pol (2^21 samples), 75 km, 17 CD taps (6 bit), "
                       "5-bit I/Q, FNT-CDC N=64 alpha=4080 S=48 + FNT-AEQ 4x4 RV-MIMO N=64 alpha=4080 K=16, "
-                      "AEQ segments 2048 sym + 512 warm-up"),
+                      "AEQ segments of 1024 symbols + 128 warm-up starting from the stream's carried taps"),
     "cfg5": dict(n_sym=1 << 26, km=80.0, n_aeq=32, alpha_aeq=2, segment=1 << 16, warmup=1 << 12,
                  desc="PDM bandwidth stress, 2^27 samples/pol, 80 km, 19 CD taps, FNT-AEQ N=32 alpha=2, "
                       "segments 2^16 + 2^12 warm-up"),
 }
 MU_SHIFT = 9
+TAP_INIT = 2048
 
 # Algorithmic integer-op model (one count per operation the method needs, at
 # its cheapest: a Z_F radix-2 butterfly = add, subtract, twiddle multiply and
@@ -174,10 +176,10 @@ def aggregate(samples_per_rank: int, world: int, max_seconds: float) -> float:
 _W = {}
 
 
-def _worker_init(x, taps, prm_kw):
+def _worker_init(x, taps, prm_kw, T0):
     import oracle
     oracle.build()
-    _W.update(x=x, taps=taps, prm=oracle.ChainParams(**prm_kw))
+    _W.update(x=x, taps=taps, prm=oracle.ChainParams(**prm_kw), T0=T0)
 
 
 def _worker_noop(i):
@@ -186,7 +188,7 @@ def _worker_noop(i):
 
 def _worker_segment(seg):
     import oracle
-    keep, out, _ = oracle.chain_segment(_W["x"], _W["taps"], _W["prm"], seg)
+    keep, out, _ = oracle.chain_segment(_W["x"], _W["taps"], _W["prm"], seg, T0=_W["T0"])
     return seg, keep, out
 
 
@@ -195,10 +197,11 @@ class OraclePool:
     of AEQ segments is timed from submission to the last result (start-up
     excluded)."""
 
-    def __init__(self, x, taps, prm_kw, procs):
+    def __init__(self, x, taps, prm_kw, procs, T0):
         import multiprocessing as mp
         self.procs = procs
-        self.pool = mp.get_context("spawn").Pool(procs, initializer=_worker_init, initargs=(x, taps, prm_kw))
+        self.pool = mp.get_context("spawn").Pool(procs, initializer=_worker_init,
+                                                 initargs=(x, taps, prm_kw, T0))
         self.pool.map(_worker_noop, range(procs), chunksize=1)
 
     def run(self, segs):
@@ -246,7 +249,9 @@ def run_fnt(args, rank, world, local_rank):
     nsym = fnt.chain_nsym(n, L)
     x = torch.from_numpy(x_np).to(dev)
     out = torch.zeros((nsym, 4), dtype=torch.int16, device=dev)
-    batch = fnt.Batch(plan, [fnt.Frame(x, out, taps)], fnt.OP_CHAIN, use_graph=False)
+    state = torch.zeros((4, 4, 16), dtype=torch.int32, device=dev)       # the stream's carried AEQ taps
+    state[[0, 1, 2, 3], [0, 1, 2, 3], 8] = TAP_INIT << 16
+    batch = fnt.Batch(plan, [fnt.Frame(x, out, taps, state)], fnt.OP_CHAIN, use_graph=False)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
@@ -295,12 +300,20 @@ def run_fnt(args, rank, world, local_rank):
     ms_per_step = total_ms / args.steps
     value = aggregate(n, world, ms_per_step * 1e-3)
 
+    # one more step from a recorded tap state: its output is what the CPU-baseline
+    # leg recomputes on sampled segments
+    state_snap = state.cpu().numpy().copy()
+    step()
+    torch.cuda.synchronize()
+    out_check = out.clone()
+
     # end to end through the public call with host buffers (pinned), copies included
     e2e = None
     if args.e2e_steps > 0:
         xh = torch.from_numpy(x_np).pin_memory()
         oh = torch.empty((nsym, 4), dtype=torch.int16).pin_memory()
-        fr = [fnt.Frame(xh, oh, taps)]
+        st_e2e = torch.from_numpy(state_snap).to(dev)
+        fr = [fnt.Frame(xh, oh, taps, st_e2e)]
         fnt.cdc_aeq_run(plan, fr, host=True)
         barrier()
         t0 = time.perf_counter()
@@ -310,8 +323,9 @@ def run_fnt(args, rank, world, local_rank):
         e2e = {"value": aggregate(n * args.e2e_steps, world, el), "unit": UNIT,
                "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(oh.numel() * 2),
                "ms_per_step": el / args.e2e_steps * 1e3, "api": "fnt_cdc_aeq_run(host_buffers=1)"}
-        if not torch.equal(oh, out.cpu()):
-            e2e["bitexact_vs_device_path"] = False
+        st_e2e.copy_(torch.from_numpy(state_snap))
+        fnt.cdc_aeq_run(plan, fr, host=True)
+        e2e["bitexact_vs_device_path"] = bool(torch.equal(oh, out_check.cpu()))
 
     # roofline of the dominant kernel
     aeq_avg = statistics.mean(aeq_ms)
@@ -347,15 +361,22 @@ def run_fnt(args, rank, world, local_rank):
         "wall_s_timed_region": round(wall, 3),
         "e2e": e2e,
     }
-    return res, (x_np, taps, out, wl)
+    return res, (x_np, taps, out_check, wl, state_snap)
 
 
-def cpu_baseline(x_np, taps, wl, out_dev=None, n_seg=96, procs=None):
+def init_taps():
+    T = np.zeros((4, 4, 16), np.int32)
+    for s_ in range(4):
+        T[s_, s_, 8] = TAP_INIT << 16
+    return T
+
+
+def cpu_baseline(x_np, taps, wl, out_dev=None, n_seg=96, procs=None, T0=None):
     """The oracle as it stands on a bounded sample: n_seg AEQ segments spread
     over the stream, in a spawn pool over the host cores."""
     procs = procs or min(os.cpu_count() or 1, n_seg)
     segs, total = _segments(x_np, taps, wl, n_seg)
-    pool = OraclePool(x_np, taps, _prm_kw(wl), procs)
+    pool = OraclePool(x_np, taps, _prm_kw(wl), procs, init_taps() if T0 is None else T0)
     try:
         secs, samples, res = pool.run(segs)
     finally:
@@ -377,7 +398,7 @@ def run_reference(args):
     frame = synth.config2(wl["n_sym"]) if args.workload == "cfg2" else synth.config5(2 * wl["n_sym"])
     procs = min(os.cpu_count() or 1, 16)
     segs, total = _segments(frame.x, frame.taps, wl, args.ref_segments)
-    pool = OraclePool(frame.x, frame.taps, _prm_kw(wl), procs)
+    pool = OraclePool(frame.x, frame.taps, _prm_kw(wl), procs, init_taps())
     try:
         for _ in range(args.warmup):
             pool.run(segs[:procs])
@@ -408,7 +429,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["fnt", "reference"], default="fnt")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cfg2")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-segments", type=int, default=96)
+    ap.add_argument("--cpu-segments", type=int, default=128)
     ap.add_argument("--ref-segments", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
@@ -427,9 +448,9 @@ def main(argv=None):
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    res, (x_np, taps, out, wl) = run_fnt(args, rank, world, local_rank)
+    res, (x_np, taps, out, wl, T0) = run_fnt(args, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(x_np, taps, wl, out, n_seg=args.cpu_segments)
+        res["cpu_baseline"] = cpu_baseline(x_np, taps, wl, out, n_seg=args.cpu_segments, T0=T0)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

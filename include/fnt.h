@@ -83,9 +83,10 @@ FNT_API const char *fnt_version(void);
  * aeq_segment        symbols per AEQ segment for long streams; 0 = one serial run
  *                    per frame.  With segments, output segment s covers symbols
  *                    [s*seg, (s+1)*seg) and its AEQ run starts aeq_warmup symbols
- *                    earlier (not before 0) from the plan's initial taps with zero
- *                    history, as if that slice were a frame of its own; only the
- *                    segment's own outputs are kept.  Segments run in parallel.
+ *                    earlier (not before 0) from the frame's initial taps (its
+ *                    state, or the plan's taps) with zero history, as if that
+ *                    slice were a frame of its own; only the segment's own
+ *                    outputs are kept.  Segments run in parallel.
  * aeq_warmup         warm-up symbols of each segment (ignored without segments).
  */
 typedef struct fnt_plan_desc {
@@ -134,8 +135,9 @@ FNT_API fnt_status fnt_plan_destroy(fnt_plan *plan);
  *             (tap = state >> 16), read at the start and overwritten with the
  *             adapted taps at the end; NULL = start from the plan's initial taps
  *             and keep nothing.  With AEQ segments every segment starts from the
- *             plan's initial taps and the state, if given, only receives the
- *             final taps of the last segment.  Ignored by the CDC.
+ *             state as it was when the call began (the library copies it first)
+ *             and the state then receives the final taps of the last segment.
+ *             Ignored by the CDC.
  *   n         samples (CDC, chain) or symbols (AEQ alone); 0 is allowed.
  *   n_pol     1 or 2 for the CDC; 2 for the chain; ignored by the AEQ alone.
  *   cd_len    L, 1..31 (31 * 2 * 16 * 32 = 31744 keeps every output inside int16

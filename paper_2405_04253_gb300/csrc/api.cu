@@ -244,8 +244,12 @@ static void add_cdc_items(const DevFrame &df, int fi, std::vector<int4> &items) 
         items.push_back(make_int4(fi, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), 0));
 }
 
-static void add_aeq_chains(const fnt_plan *p, const DevFrame &df, int fi, const int32_t *init_dev,
-                           std::vector<AeqChain> &chains) {
+// AEQ runs of one frame.  Unsegmented: one chain that reads and writes the
+// frame's state (or starts from the plan's taps).  Segmented: every segment
+// starts from the frame's state as it was when the call began (a copy taken on
+// the stream first, since the last segment overwrites the state) or from the
+// plan's taps; only the last segment writes the state.
+static void add_aeq_chains(const fnt_plan *p, const DevFrame &df, int fi, const int32_t *init_dev, Work &w) {
     const int64_t n = df.n_sym;
     if (n == 0) return;
     const int64_t seg = p->d.aeq_segment;
@@ -257,8 +261,14 @@ static void add_aeq_chains(const fnt_plan *p, const DevFrame &df, int fi, const 
         c.keep = 0;
         c.end = n;
         c.init = df.state ? df.state : init_dev;
-        chains.push_back(c);
+        c.init_copy = -1;
+        w.chains.push_back(c);
         return;
+    }
+    int copy = -1;
+    if (df.state) {
+        copy = (int)w.init_src.size();
+        w.init_src.push_back(fi);
     }
     for (int64_t k = 0; k < n; k += seg) {
         AeqChain c{};
@@ -268,7 +278,8 @@ static void add_aeq_chains(const fnt_plan *p, const DevFrame &df, int fi, const 
         c.begin = std::max<int64_t>(0, k - p->d.aeq_warmup);
         c.write_state = (df.state != nullptr) && c.end == n;
         c.init = init_dev;
-        chains.push_back(c);
+        c.init_copy = copy;
+        w.chains.push_back(c);
     }
 }
 
@@ -290,7 +301,7 @@ fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work 
     w.scratch_bytes = scratch;
     for (int i = 0; i < b->n_frames; ++i) {
         if (op != FNT_OP_AEQ) add_cdc_items(w.frames[i], i, w.items);
-        if (op != FNT_OP_CDC) add_aeq_chains(p, w.frames[i], i, p->d_init, w.chains);
+        if (op != FNT_OP_CDC) add_aeq_chains(p, w.frames[i], i, p->d_init, w);
     }
     // longest chains first: they bound the makespan of the serial AEQ recurrences
     std::stable_sort(w.chains.begin(), w.chains.end(), [](const AeqChain &a, const AeqChain &c) {
@@ -307,7 +318,8 @@ void layout(Work &w) {
     w.off_frames = 0;
     w.off_items = up(w.off_frames + w.frames.size() * sizeof(DevFrame));
     w.off_chains = up(w.off_items + w.items.size() * sizeof(int4));
-    w.off_scratch = up(w.off_chains + w.chains.size() * sizeof(AeqChain));
+    w.off_init = up(w.off_chains + w.chains.size() * sizeof(AeqChain));
+    w.off_scratch = up(w.off_init + w.init_src.size() * kStateBytes);
     w.total = up(w.off_scratch + (size_t)w.scratch_bytes);
     if (w.total == 0) w.total = 256;
 }
@@ -318,6 +330,8 @@ fnt_status upload_work(Work &w, char *dev, cudaStream_t stream) {
     if (w.op == FNT_OP_CHAIN)
         for (size_t i = 0; i < w.frames.size(); ++i)
             w.frames[i].aeq_in = (int8_t *)(dev + w.off_scratch + w.scratch_off[i]);
+    for (AeqChain &c : w.chains)
+        if (c.init_copy >= 0) c.init = (const int32_t *)(dev + w.off_init + (size_t)c.init_copy * kStateBytes);
     cudaError_t e;
     if (!w.frames.empty()) {
         e = cudaMemcpyAsync(dev + w.off_frames, w.frames.data(), w.frames.size() * sizeof(DevFrame),
@@ -355,6 +369,11 @@ fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaSt
         if (e != cudaSuccess) return cuda_fail(e, "cdc kernel launch");
     }
     if ((stages & 2) && w.op != FNT_OP_CDC && !w.chains.empty()) {
+        for (size_t k = 0; k < w.init_src.size(); ++k) {
+            cudaError_t e = cudaMemcpyAsync((void *)(dev + w.off_init + k * kStateBytes), w.frames[w.init_src[k]].state,
+                                            kStateBytes, cudaMemcpyDeviceToDevice, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "copy initial taps");
+        }
         const int nw = p->aeq_warps;
         const int n = (int)w.chains.size();
         AeqParams prm{p->d.mu_shift, p->d.rde_a};

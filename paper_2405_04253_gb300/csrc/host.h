@@ -35,9 +35,12 @@ struct Work {
     std::vector<int4> items;          // CDC: (frame, first block, blocks)
     std::vector<AeqChain> chains;     // AEQ runs, longest first
     std::vector<int64_t> scratch_off; // chain: per-frame offset of the intermediate buffer
+    std::vector<int> init_src;        // segmented frames with a state: frame whose state is copied
     int64_t scratch_bytes = 0;
-    size_t off_frames = 0, off_items = 0, off_chains = 0, off_scratch = 0, total = 0;
+    size_t off_frames = 0, off_items = 0, off_chains = 0, off_init = 0, off_scratch = 0, total = 0;
 };
+
+constexpr size_t kStateBytes = 16 * kAeqK * sizeof(int32_t);
 
 fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work &w);
 void layout(Work &w);

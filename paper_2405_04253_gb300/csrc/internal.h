@@ -36,8 +36,11 @@ struct alignas(16) AeqChain {
     int64_t begin;         // first symbol the run processes (history is zero before it)
     int64_t keep;          // first symbol whose output is stored
     int64_t end;           // one past the last symbol
-    const int32_t *init;   // initial taps (frame state or the plan's initial taps)
+    const int32_t *init;   // initial taps (frame state, a copy of it, or the plan's initial taps)
+    int32_t init_copy;     // host side only: index of the state copy `init` must point to, or -1
+    int32_t pad0;
 };
+static_assert(sizeof(AeqChain) == 48, "AeqChain layout");
 
 struct AeqParams {
     int32_t mu_shift;

@@ -39,7 +39,8 @@ constexpr int kMaxChains = FNT_NOALLOC_MAX_SEGMENTS;
 constexpr size_t kOffFrame = 0;
 constexpr size_t kOffItems = 256;
 constexpr size_t kOffChains = kOffItems + ((size_t)kMaxItems * sizeof(int4) + 255) / 256 * 256;
-constexpr size_t kOffSym = kOffChains + ((size_t)kMaxChains * sizeof(AeqChain) + 255) / 256 * 256;
+constexpr size_t kOffInit = kOffChains + ((size_t)kMaxChains * sizeof(AeqChain) + 255) / 256 * 256;
+constexpr size_t kOffSym = kOffInit + (kStateBytes + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kOffSym + (size_t)kMaxSym * 4;
 
 constexpr int kMaxDevices = 64;
@@ -47,7 +48,8 @@ constexpr int kMaxDevices = 64;
 }  // namespace
 }  // namespace fnt
 
-// The scratch: frame descriptor, CDC work items, AEQ chains, intermediate symbols.
+// The scratch: frame descriptor, CDC work items, AEQ chains, a copy of the
+// initial taps, intermediate symbols.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[fnt::kScratchBytes];
 
 namespace fnt {
@@ -132,6 +134,7 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
         c.write_state = f->aeq_state != nullptr;
         c.end = nsym;
         c.init = f->aeq_state ? f->aeq_state : p->d_init;
+        c.init_copy = -1;
     } else {
         for (int64_t k = 0; k < nsym; k += seg) {
             AeqChain &c = g_chains[nc++];
@@ -140,7 +143,9 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
             c.end = std::min(nsym, k + seg);
             c.begin = std::max<int64_t>(0, k - p->d.aeq_warmup);
             c.write_state = (f->aeq_state != nullptr) && c.end == nsym;
-            c.init = p->d_init;
+            // segments start from the state as it was at the call (copied below)
+            c.init = f->aeq_state ? (const int32_t *)(base + kOffInit) : p->d_init;
+            c.init_copy = -1;
         }
         // segments are all equal but the last, so they need no longest-first sort
     }
@@ -158,6 +163,10 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
                    std::min((n_items + nw - 1) / nw, p->n_sm * 64), stream);
     if (e != cudaSuccess) return cuda_fail(e, "noalloc: cdc kernel launch");
     if (nc > 0) {
+        if (n_chains > 1 && f->aeq_state) {
+            e = cudaMemcpyAsync(base + kOffInit, f->aeq_state, kStateBytes, cudaMemcpyDeviceToDevice, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "noalloc: copy initial taps");
+        }
         AeqParams prm{p->d.mu_shift, p->d.rde_a};
         e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(base + kOffChains), nc, prm, p->aeq_warps, 0, stream);
         if (e != cudaSuccess) return cuda_fail(e, "noalloc: aeq kernel launch");

@@ -202,6 +202,7 @@ fnt_status launch_wave(fnt_session *ss, Slot &slot) {
             c.keep = 0;
             c.end = r.n_sym;
             c.init = df.state;
+            c.init_copy = -1;
             w.chains.push_back(c);
         }
     }

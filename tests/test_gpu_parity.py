@@ -156,12 +156,37 @@ def test_aeq_segmented_matches_oracle(orc, na, alpha):
     rng = np.random.default_rng(5)
     x = rng.integers(-16, 16, (5000, 4)).astype(np.int8)
     plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=9, aeq_segment=700, aeq_warmup=150)
-    T = np.zeros((4, 4, 16), np.int32)
-    got, Tg = run_aeq(plan, x, T)
-    ref, Tr = orc.aeq_segmented(x, orc.aeq_init_taps(16, 2048), na, alpha, mu_shift=9, rde_a=64,
-                                seg_len=700, warmup=150)
+    T0 = orc.aeq_init_taps(16, 2048) + rng.integers(-(1 << 22), 1 << 22, (4, 4, 16)).astype(np.int32)
+    # segments start from the state as it was at the call; the state ends with the last segment's taps
+    got, Tg = run_aeq(plan, x, T0)
+    ref, Tr = orc.aeq_segmented(x, T0, na, alpha, mu_shift=9, rde_a=64, seg_len=700, warmup=150)
     assert np.array_equal(got, ref)
     assert np.array_equal(Tg, Tr)
+    # without a state every segment starts from the plan's taps
+    got2, _ = run_aeq(plan, x, None)
+    ref2, _ = orc.aeq_segmented(x, orc.aeq_init_taps(16, 2048), na, alpha, mu_shift=9, rde_a=64,
+                                seg_len=700, warmup=150)
+    assert np.array_equal(got2, ref2)
+
+
+def test_chain_segmented_state_carried_over_calls(orc):
+    """A long stream processed call after call: each call's segments start from
+    the taps the previous call ended with."""
+    f = synth.config2(1 << 13)
+    kw = dict(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=1024, aeq_warmup=128)
+    plan = F.Plan(**kw)
+    prm = orc.ChainParams(n_aeq=64, alpha_aeq=4080, mu_shift=9, seg_len=1024, warmup=128)
+    xd = dev(f.x)
+    T = orc.aeq_init_taps(16, 2048)
+    st = dev(T)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    b = F.Batch(plan, [F.Frame(xd, i16((nsym, 4)), f.taps, st)], F.OP_CHAIN, use_graph=True)
+    for call in range(3):
+        b.launch()
+        torch.cuda.synchronize()
+        ref, T = orc.chain(f.x, f.taps, prm, T0=T)
+        assert np.array_equal(b.frames[0].out.cpu().numpy(), ref), call
+        assert np.array_equal(st.cpu().numpy(), T), call
 
 
 # ------------------------------------------------------------------- chain -----
@@ -232,3 +257,30 @@ def test_chain_host_buffers_equal_device(orc):
     F.cdc_aeq_run(plan, [F.Frame(np.ascontiguousarray(f.x), host_out, f.taps)], host=True)
     ref, _ = oracle_chain(orc, f.x, f.taps, mu_shift=9)
     assert np.array_equal(host_out, ref)
+
+
+def test_chain_full_size_cfg2_sampled_segments(orc):
+    """The benchmark's workload at full size (2^21 samples per polarisation,
+    segments of 1024 + 128, carried state), launched as bench.py launches it;
+    sampled segments recomputed one by one by the oracle."""
+    f = synth.config2()
+    assert f.x.shape == (1 << 21, 2, 2)
+    plan = F.Plan(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=1024, aeq_warmup=128)
+    prm = orc.ChainParams(n_aeq=64, alpha_aeq=4080, mu_shift=9, seg_len=1024, warmup=128)
+    T0 = orc.aeq_init_taps(16, 2048)
+    st = dev(T0)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    out = i16((nsym, 4))
+    b = F.Batch(plan, [F.Frame(dev(f.x), out, f.taps, st)], F.OP_CHAIN, use_graph=False)
+    b.launch_stage(0)
+    b.launch_stage(1)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    n_seg = (nsym + 1023) // 1024
+    rng = np.random.default_rng(2)
+    segs = sorted({0, 1, n_seg // 2, n_seg - 2, n_seg - 1, *rng.integers(0, n_seg, 15).tolist()})
+    for s in segs:
+        keep, ref, Tend = orc.chain_segment(f.x, f.taps, prm, s, T0=T0)
+        assert np.array_equal(got[keep:keep + ref.shape[0]], ref), s
+        if s == n_seg - 1:
+            assert np.array_equal(st.cpu().numpy(), Tend)

@@ -34,6 +34,17 @@ def test_noalloc_equals_allocating_entry_point_twice_segmented():
         F.cdc_aeq_run_noalloc(plan, F.Frame(x, out, f.taps))
         torch.cuda.synchronize()
         assert torch.equal(out, ref)
+    # segments starting from a carried tap state, two calls in a row
+    init = torch.zeros((4, 4, 16), dtype=torch.int32, device="cuda")
+    init[[0, 1, 2, 3], [0, 1, 2, 3], 8] = 2048 << 16
+    st_ref, st_new = init.clone(), init.clone()
+    for call in range(2):
+        ref, out = _poison(nsym), _poison(nsym)
+        F.cdc_aeq_run(plan, [F.Frame(x, ref, f.taps, st_ref)])
+        F.cdc_aeq_run_noalloc(plan, F.Frame(x, out, f.taps, st_new))
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), call
+        assert torch.equal(st_new, st_ref), call
 
 
 def test_noalloc_equals_allocating_entry_point_twice_with_state():
