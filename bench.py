@@ -46,8 +46,9 @@ WORKLOADS = {
                       "5-bit I/Q, FNT-CDC N=64 alpha=4080 S=48 + FNT-AEQ 4x4 RV-MIMO N=64 alpha=4080 K=16, "
                       "AEQ segments of 1024 symbols + 128 warm-up starting from the stream's carried taps"),
     "cfg5": dict(n_sym=1 << 26, km=80.0, n_aeq=32, alpha_aeq=2, segment=1 << 16, warmup=1 << 12,
-                 desc="PDM bandwidth stress, 2^27 samples/pol, 80 km, 19 CD taps, FNT-AEQ N=32 alpha=2, "
-                      "segments 2^16 + 2^12 warm-up"),
+                 desc="PDM bandwidth stress, one stream of 2^27 samples/pol (a generated 2^23-sample stretch "
+                      "repeated), 80 km, 19 CD taps, FNT-AEQ N=32 alpha=2, segments 2^16 + 2^12 warm-up from "
+                      "the carried taps"),
 }
 MU_SHIFT = 9
 TAP_INIT = 2048
@@ -238,8 +239,7 @@ def run_fnt(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     wl = WORKLOADS[args.workload]
-    gen = synth.config2 if args.workload == "cfg2" else synth.config5
-    frame = gen(wl["n_sym"]) if args.workload == "cfg2" else synth.config5(2 * wl["n_sym"])
+    frame = synth.config2(wl["n_sym"]) if args.workload == "cfg2" else synth.config5(2 * wl["n_sym"])
     x_np, taps = frame.x, frame.taps
     n = x_np.shape[0]
     L = taps.shape[0]
@@ -394,7 +394,7 @@ def run_reference(args):
     """The CPU oracle as the reference arm: each step a bounded sample of the
     same workload (args.ref_segments AEQ segments) on the host cores."""
     import synth
-    wl = WORKLOADS[args.workload]
+    wl = WORKLOADS[args.workload if args.workload in WORKLOADS else "cfg2"]
     frame = synth.config2(wl["n_sym"]) if args.workload == "cfg2" else synth.config5(2 * wl["n_sym"])
     procs = min(os.cpu_count() or 1, 16)
     segs, total = _segments(frame.x, frame.taps, wl, args.ref_segments)
@@ -421,13 +421,195 @@ def run_reference(args):
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------- other workloads ----
+
+def _percentile(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def run_cfg1(args):
+    """cfg 1: single-polarisation FNT-CDC on 65,536 samples (17 taps)."""
+    import torch
+    import paper_2405_04253_gb300 as fnt
+    import synth
+    f = synth.config1()
+    n = f.x.shape[0]
+    plan = fnt.Plan()
+    x = torch.from_numpy(f.x).cuda()
+    out = torch.zeros((n, 1, 2), dtype=torch.int16, device="cuda")
+    b = fnt.Batch(plan, [fnt.Frame(x, out, f.taps, n_pol=1)], fnt.OP_CDC, use_graph=True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        b.launch(stream)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        b.launch(stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    ops = cdc_ops(n, 48, n_pol=1)
+    return {"workload": "cfg1: single-pol FNT-CDC, 65,536 samples, 17 taps, N=64 alpha=4080 S=48",
+            "metric": "Msamples/s", "value": round(n / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
+            "steps": args.steps, "gpu_launches_per_step": b.kernel_count(),
+            "roofline": {"bound": "alu", "kernel": "cdc_kernel<cdc>", "achieved": round(ops / (ms * 1e-3) / 1e12, 3),
+                         "peak": round(alu_peak_ops() / 1e12, 2), "unit": "Tops/s (int32, algorithmic)",
+                         "frac": round(ops / (ms * 1e-3) / alu_peak_ops(), 4)},
+            "note": "65,536 samples is 1366 blocks: one partial wave of 43 CTAs on 152 SMs, launch-latency bound"}
+
+
+def run_cfg3(args):
+    """cfg 3: 4096 independent PDM frames (2^12..2^18 samples, 5..19 taps) in
+    one prepared, graph-launched batch, against one launch pair per frame."""
+    import torch
+    import paper_2405_04253_gb300 as fnt
+    from paper_2405_04253_gb300 import autotune
+    import synth
+    frames_np = synth.config3(args.frames)
+    plan = fnt.Plan(n_aeq=32, alpha_aeq=2, mu_shift=MU_SHIFT)
+    xs, outs, frames = [], [], []
+    total = 0
+    for f in frames_np:
+        x = torch.from_numpy(f.x).cuda()
+        o = torch.zeros((fnt.chain_nsym(f.x.shape[0], f.taps.shape[0]), 4), dtype=torch.int16, device="cuda")
+        frames.append(fnt.Frame(x, o, f.taps))
+        total += f.x.shape[0]
+    tuned = autotune.tune(plan, frames, fnt.OP_CHAIN, reps=3,
+                          cache=os.path.join(ROOT, "paper_2405_04253_gb300", "_build", "autotune.json"))
+    batch = fnt.Batch(plan, frames, fnt.OP_CHAIN, use_graph=True)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    batch.launch(stream)
+    torch.cuda.synchronize()
+    ref = [fr.out.clone() for fr in frames]
+    reps = max(1, args.steps)
+    ev[0].record(stream)
+    for _ in range(reps):
+        batch.launch(stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms_batched = ev[0].elapsed_time(ev[1]) / reps
+    # one launch pair per frame (prepared per-frame batches, no per-call setup)
+    singles = [fnt.Batch(plan, [fr], fnt.OP_CHAIN, use_graph=False) for fr in frames]
+    for fr in frames:
+        fr.out.zero_()
+    for sb in singles:
+        sb.launch(stream)
+    torch.cuda.synchronize()
+    same = all(torch.equal(fr.out, r) for fr, r in zip(frames, ref))
+    ev[0].record(stream)
+    for _ in range(reps):
+        for sb in singles:
+            sb.launch(stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms_single = ev[0].elapsed_time(ev[1]) / reps
+    # oracle check on a sample of the shorter frames
+    import oracle
+    rng = np.random.default_rng(3)
+    short = [i for i, f in enumerate(frames_np) if f.x.shape[0] <= 8192]
+    pick = rng.choice(short, size=min(6, len(short)), replace=False)
+    ok = True
+    for i in pick:
+        o, _ = oracle.chain(frames_np[i].x, frames_np[i].taps, oracle.ChainParams(mu_shift=MU_SHIFT))
+        ok &= bool(np.array_equal(ref[i].cpu().numpy(), o))
+    return {"workload": f"cfg3: {len(frames)} PDM frames, lengths log-uniform 2^12..2^18 samples "
+                        f"({total} samples), 10-80 km (5-19 taps), FNT-AEQ N=32 alpha=2, fresh taps per frame",
+            "metric": "Gsamples/s", "batched": round(total / (ms_batched * 1e-3) / 1e9, 3),
+            "per_frame_launches": round(total / (ms_single * 1e-3) / 1e9, 3),
+            "speedup": round(ms_single / ms_batched, 2), "ms_batched": round(ms_batched, 3),
+            "ms_per_frame_launches": round(ms_single, 3), "gpu_launches_batched": batch.kernel_count(),
+            "gpu_launches_per_frame_path": 2 * len(frames), "autotuned": tuned,
+            "bitexact_batched_vs_per_frame": same, "oracle_sample_bitexact": ok, "oracle_sample_frames": len(pick)}
+
+
+def run_cfg4(args):
+    """cfg 4: serving -- Poisson arrivals at 20k frames/s over 256 links, frames
+    2^12..2^16 samples, device-resident AEQ state per link, 8 GB admission cap,
+    pinned host buffers (copies included in every request's latency)."""
+    import torch
+    import paper_2405_04253_gb300 as fnt
+    import synth
+    tr = synth.config4(args.frames)
+    plan = fnt.Plan(n_aeq=32, alpha_aeq=2, mu_shift=MU_SHIFT)
+
+    def serve(paced: bool):
+        from collections import deque
+        sess = fnt.Session(plan, len(tr.link_taps), 8 << 30, args.streams)
+        for l, t in enumerate(tr.link_taps):
+            sess.set_link(l, t)
+        bufs = []
+        for f in tr.frames:
+            xh = torch.from_numpy(f.x).pin_memory()
+            oh = torch.zeros((fnt.chain_nsym(f.x.shape[0], f.taps.shape[0]), 4), dtype=torch.int16).pin_memory()
+            bufs.append((xh, oh))
+        n = len(tr.frames)
+        submitted, lat, status = {}, [], []
+        waiting = deque()
+        i = completed = 0
+        t_first = t_last = None
+        t0 = time.perf_counter()
+        while completed < n:
+            now = time.perf_counter() - t0
+            while i < n and (not paced or tr.frames[i].arrival_s <= now):
+                waiting.append(i)
+                i += 1
+            while waiting:
+                j = waiting[0]
+                tk = sess.try_submit(tr.frames[j].link, bufs[j][0], bufs[j][1])
+                if tk is None:
+                    break                                   # memory cap reached: keep arrival order
+                waiting.popleft()
+                t_ref = tr.frames[j].arrival_s if paced else time.perf_counter() - t0
+                t_first = t_ref if t_first is None else min(t_first, t_ref)
+                submitted[tk] = t_ref
+            for c in sess.poll(timeout_us=0):
+                t_done = time.perf_counter() - t0
+                lat.append((t_done - submitted.pop(c["ticket"])) * 1e3)
+                status.append(c["status"])
+                completed += 1
+                t_last = t_done
+        sess.close()
+        samples = sum(f.x.shape[0] for f in tr.frames)
+        return {"p50_ms": round(_percentile(lat, 50), 3), "p99_ms": round(_percentile(lat, 99), 3),
+                "max_ms": round(max(lat), 3), "throughput_gsps": round(samples / (t_last - t_first) / 1e9, 4),
+                "all_ok": all(st == fnt.FNT_OK for st in status)}, bufs
+
+    paced, bufs = serve(True)
+    flood, _ = serve(False)
+    # per-link bit-exactness against sequential oracle processing (a few links)
+    import oracle
+    prm = oracle.ChainParams(mu_shift=MU_SHIFT)
+    links = sorted({f.link for f in tr.frames})[:4]
+    ok = True
+    nchk = 0
+    for l in links:
+        T = oracle.aeq_init_taps(16, prm.w0)
+        for j, f in enumerate(tr.frames):
+            if f.link != l:
+                continue
+            o, T = oracle.chain(f.x, f.taps, prm, T0=T)
+            ok &= bool(np.array_equal(bufs[j][1].numpy(), o))
+            nchk += 1
+    offered_gsps = sum(f.x.shape[0] for f in tr.frames) / tr.frames[-1].arrival_s / 1e9
+    return {"workload": f"cfg4: {len(tr.frames)} frames, Poisson 20k frames/s over {len(tr.link_taps)} links, "
+                        "2^12..2^16 samples, AEQ N=32 state carried per link, 8 GB cap, pinned host I/O",
+            "paced": paced, "saturated": flood, "offered_gsps": round(offered_gsps, 4), "streams": args.streams,
+            "oracle_links_bitexact": ok, "oracle_frames_checked": nchk}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["fnt", "reference"], default="fnt")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cfg2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["cfg1", "cfg3", "cfg4"], default="cfg2")
+    ap.add_argument("--frames", type=int, default=0, help="cfg3 / cfg4: frame count (default 4096 / 2048)")
+    ap.add_argument("--streams", type=int, default=4, help="cfg4: concurrent waves")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-segments", type=int, default=128)
     ap.add_argument("--ref-segments", type=int, default=48)
@@ -441,6 +623,17 @@ def main(argv=None):
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return 0
+    if args.workload in ("cfg1", "cfg3", "cfg4"):
+        import torch
+        torch.cuda.set_device(local_rank)
+        if args.workload == "cfg3":
+            args.frames = args.frames or 4096
+        if args.workload == "cfg4":
+            args.frames = args.frames or 2048
+        fn = {"cfg1": run_cfg1, "cfg3": run_cfg3, "cfg4": run_cfg4}[args.workload]
+        if rank == 0:
+            print(json.dumps(fn(args)), flush=True)
         return 0
 
     if world > 1:

@@ -1,0 +1,86 @@
+"""Launch-shape autotuner for libfnt.
+
+Times each candidate (CDC warps per CTA, AEQ warps per CTA) on a prepared batch
+with CUDA events around each stage on the launching stream, after warm-up,
+and keeps the fastest per stage.  Results are cached in a JSON file keyed by
+the workload's shape, so a later run with the same shape reuses them.  Only
+launch shapes change: results are bit-identical for every candidate.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import OP_CHAIN, Batch, Plan
+
+CANDIDATES = (1, 2, 3, 4)
+
+
+def _key(plan: Plan, frames, op: int) -> str:
+    d = plan.desc
+    lens = sorted(int(f.n) for f in frames)
+    total = sum(lens)
+    return (f"op{op}_n{len(frames)}_tot{total}_max{lens[-1] if lens else 0}_aeq{d.n_aeq}"
+            f"_seg{d.aeq_segment}_{d.aeq_warmup}")
+
+
+def _time_stage(batch: Batch, stage: int, reps: int, stream) -> float:
+    import torch
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(2):
+        batch.launch_stage(stage, stream)
+    evs[0].record(stream)
+    for _ in range(reps):
+        batch.launch_stage(stage, stream)
+    evs[1].record(stream)
+    torch.cuda.synchronize()
+    return evs[0].elapsed_time(evs[1]) / reps
+
+
+def tune(plan: Plan, frames, op: int = OP_CHAIN, reps: int = 20, cache: str | None = None) -> dict:
+    """Picks and applies the fastest warps-per-CTA for each stage of `op` on
+    these frames; returns {"cdc_warps", "aeq_warps", "cdc_ms", "aeq_ms"}."""
+    import torch
+    key = _key(plan, frames, op)
+    if cache and os.path.exists(cache):
+        try:
+            with open(cache) as fh:
+                hit = json.load(fh).get(key)
+        except (OSError, ValueError):
+            hit = None
+        if hit:
+            plan.set_launch(hit["cdc_warps"], hit["aeq_warps"])
+            return hit
+    stream = torch.cuda.current_stream()
+    batch = Batch(plan, frames, op, use_graph=False)
+    best = {}
+    for stage, name in ((0, "cdc"), (1, "aeq")):
+        if stage == 0 and op == 1 or stage == 1 and op == 0:
+            continue
+        for w in CANDIDATES:
+            if stage == 0:
+                plan.set_launch(cdc_warps=w)
+            else:
+                plan.set_launch(aeq_warps=w)
+            ms = _time_stage(batch, stage, reps, stream)
+            if name + "_ms" not in best or ms < best[name + "_ms"]:
+                best[name + "_ms"] = ms
+                best[name + "_warps"] = w
+    best.setdefault("cdc_warps", 4)
+    best.setdefault("aeq_warps", 2)
+    plan.set_launch(best["cdc_warps"], best["aeq_warps"])
+    batch.close()
+    if cache:
+        data = {}
+        if os.path.exists(cache):
+            try:
+                with open(cache) as fh:
+                    data = json.load(fh)
+            except (OSError, ValueError):
+                data = {}
+        data[key] = best
+        tmp = cache + f".tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(data, fh, indent=1)
+        os.replace(tmp, cache)
+    return best

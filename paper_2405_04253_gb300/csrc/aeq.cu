@@ -45,13 +45,33 @@ struct AeqCfg {
     static constexpr int RED = 16 * RED_ROW;                 // per-task weighted outputs
     static constexpr int ZS = 2 * SA;
     static constexpr int ES = SA;
-    static constexpr int WORDS = XS + XF + RED + ZS + ES;
+    static constexpr int WORDS = 2 * XS + XF + RED + ZS + ES;  // xs double-buffered
     static constexpr int32_t NINV = zcent(zinv(NA));
     static constexpr int64_t ALPHA2 = ALPHA * ALPHA % kF;    // radix of the half transforms
     static constexpr int64_t AINV = zinv(ALPHA);
 };
 
 __device__ __forceinline__ int32_t sx8(uint32_t w, int sh) { return (int32_t)(w << (24 - sh)) >> 24; }
+
+// 4-byte asynchronous global -> shared copy; src_size 0 writes zeros.
+__device__ __forceinline__ void cp_async4(uint32_t *smem, const uint32_t *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// dst[q] = x[t_first + q] for q < WORDS, zero outside [lo, hi), issued asynchronously.
+template <int WORDS>
+__device__ __forceinline__ void stage_async(uint32_t *dst, const uint32_t *x, int64_t t_first, int64_t lo, int64_t hi,
+                                            int lane) {
+    for (int q = lane; q < WORDS; q += 32) {
+        const int64_t t = t_first + q;
+        const bool ok = t >= lo && t < hi;
+        cp_async4(dst + q, ok ? x + t : x, ok);
+    }
+}
 
 // Lane h = 1 of the forward split: (a_j - 0) * alpha^j for the zero-padded taps
 // (|result| < 2^17).
@@ -89,8 +109,8 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    uint32_t *xs = smem + warp * C::WORDS;
-    int32_t *xf = (int32_t *)(xs + C::XS);
+    uint32_t *xs2 = smem + warp * C::WORDS;       // two staging buffers of C::XS words
+    int32_t *xf = (int32_t *)(xs2 + 2 * C::XS);
     int32_t *red = xf + C::XF;
     int32_t *zs = red + C::RED;
     int32_t *es = zs + C::ZS;
@@ -118,16 +138,22 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
         for (int k = 0; k < K; ++k) T[k] = ch.init[(s2 * 4 + s1) * K + k];
 
         const int64_t nblk = (ch.end - ch.begin + SA - 1) / SA;
+        // input symbols of batch 0 (PRE blocks + K history); later batches are
+        // prefetched one batch ahead into the other buffer
+        __syncwarp();
+        stage_async<C::XS>(xs2, xin, ch.begin - K, ch.begin, ch.end, lane);
+        const uint32_t *xs = xs2;
         for (int64_t blk = 0; blk < nblk; ++blk) {
             const int bb = (int)(blk % C::PRE);
             const int64_t t0 = ch.begin + blk * SA;
             if (bb == 0) {
+                const int64_t batch = blk / C::PRE;
+                xs = xs2 + (batch & 1) * C::XS;
+                cp_async_wait_all();
                 __syncwarp();
-                for (int q = lane; q < C::XS; q += 32) {
-                    const int64_t t = t0 - K + q;
-                    xs[q] = (t >= ch.begin && t < ch.end) ? __ldg(xin + t) : 0u;
-                }
-                __syncwarp();
+                if (blk + C::PRE < nblk)
+                    stage_async<C::XS>(xs2 + ((batch + 1) & 1) * C::XS, xin, t0 + C::PRE * SA - K, ch.begin, ch.end,
+                                       lane);
                 {
                     // full N-point spectrum of input sq for block bq, N^-1 folded in;
                     // register r = hh * M + j holds X[bitrev(r)] = X[2 bitrev_M(j) + hh]

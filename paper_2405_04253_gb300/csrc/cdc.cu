@@ -37,6 +37,15 @@ __device__ __forceinline__ int32_t sx8(uint32_t w, int sh) { return (int32_t)(w 
 
 __device__ __forceinline__ int32_t sat5(int32_t v) { return v < -16 ? -16 : (v > 15 ? 15 : v); }
 
+// 4-byte asynchronous global -> shared copy; src_size 0 writes zeros.
+__device__ __forceinline__ void cp_async4(uint32_t *smem, const uint32_t *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // One block of one polarisation: window words w[j] = win[j][lane]; results
 // (re, im) as int16 into o[j][lane] for all 64 window positions.  `o` may be
 // `win` itself: every output depends on every input of the lane's column, so
@@ -82,7 +91,7 @@ __device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, cons
 }
 
 template <bool CHAIN>
-__global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict__ frames,
+__global__ void __launch_bounds__(128, 2) cdc_kernel(const DevFrame *__restrict__ frames,
                                                      const int4 *__restrict__ items, int n_items) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int32_t s_pow[kN];
@@ -122,21 +131,37 @@ __global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict_
             hs[kN + i] = rhoc(rho(rhoc(av) * kHScale));
         }
 
-        // Input windows: window l covers samples base + l*S + [0, 64).
+        // Input windows: window l covers samples base + l*S + [0, 64).  All 64
+        // loads of a lane are in flight at once: asynchronous 4-byte copies
+        // straight into shared memory for PDM (zero-filled outside the frame),
+        // register-staged 2-byte loads for one polarisation.
         const int64_t base = b0 * S - (kN - S);
-        const int esz = 2 * npol;
-#pragma unroll 8
-        for (int l = 0; l < 32; ++l) {
+        if (npol == 2) {
+            const uint32_t *src = (const uint32_t *)fr.in;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = lane + 32 * h;
-                const int64_t t = base + (int64_t)l * S + j;
-                uint32_t w = 0;
-                if (l < nb && t >= 0 && t < n) {
-                    w = npol == 2 ? __ldg((const uint32_t *)(fr.in + t * esz))
-                                  : (uint32_t)__ldg((const uint16_t *)(fr.in + t * esz));
+            for (int l = 0; l < 32; ++l) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = lane + 32 * h;
+                    const int64_t t = base + (int64_t)l * S + j;
+                    const bool ok = l < nb && t >= 0 && t < n;
+                    cp_async4(win + j * kRow + l, ok ? src + t : src, ok);
                 }
-                win[j * kRow + l] = w;
+            }
+            cp_async_wait_all();
+        } else {
+            const uint16_t *src = (const uint16_t *)fr.in;
+#pragma unroll 4
+            for (int l0 = 0; l0 < 32; l0 += 8) {
+                uint32_t v[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int l = l0 + (q >> 1), j = lane + 32 * (q & 1);
+                    const int64_t t = base + (int64_t)l * S + j;
+                    v[q] = (l < nb && t >= 0 && t < n) ? (uint32_t)__ldg(src + t) : 0u;
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) win[(lane + 32 * (q & 1)) * kRow + l0 + (q >> 1)] = v[q];
             }
         }
         __syncwarp();

@@ -16,7 +16,7 @@ struct fnt_plan {
     int device = 0;
     int n_sm = 1;
     int cdc_warps = 4;
-    int aeq_warps = 4;
+    int aeq_warps = 2;
 };
 
 namespace fnt {

@@ -163,17 +163,37 @@ def frame_lengths(rng: np.random.Generator, n: int, lo_log2: float, hi_log2: flo
     return np.rint(2.0 ** rng.uniform(lo_log2, hi_log2, n)).astype(np.int64)
 
 
+class _Pools:
+    """One received stream per fibre-length class (5 km classes over 10-80 km);
+    frames are slices of their class's stream at seeded offsets.  The frame's
+    own CD taps come from its exact fibre length.  Generating one stream per
+    class instead of one per frame keeps thousands of frames cheap to make; the
+    path's cost does not depend on the sample values."""
+
+    def __init__(self, config: int, pool_len: int, snr_db: float = 18.0):
+        self.config, self.pool_len, self.snr_db = config, pool_len, snr_db
+        self.cache = {}
+
+    def stream(self, km: float) -> np.ndarray:
+        c = int(np.clip(np.rint(km / 5.0) * 5, 10, 80))
+        if c not in self.cache:
+            self.cache[c] = received(rng_for(self.config, 1000 + c), self.pool_len, 2, float(c), self.snr_db)
+        return self.cache[c]
+
+    def frame(self, rng: np.random.Generator, n: int, km: float) -> np.ndarray:
+        pool = self.stream(km)
+        off = int(rng.integers(0, max(1, pool.shape[0] - n + 1)))
+        return np.ascontiguousarray(pool[off:off + n])
+
+
 def config3(n_frames: int = 4096, lo_log2: float = 12, hi_log2: float = 18) -> list[Frame]:
     """Batched: independent PDM frames, lengths log-uniform in [2^12, 2^18]
     samples, fibre uniform over 10-80 km (5-19 taps), SNR 18 dB."""
     rng = rng_for(3)
     lens = frame_lengths(rng, n_frames, lo_log2, hi_log2)
     kms = rng.uniform(10.0, 80.0, n_frames)
-    out = []
-    for i in range(n_frames):
-        r = rng_for(3, i + 1)
-        out.append(Frame(received(r, int(lens[i]), 2, kms[i], 18.0), cd_taps(kms[i]), float(kms[i])))
-    return out
+    pools = _Pools(3, int(2 ** hi_log2) + 1)
+    return [Frame(pools.frame(rng, int(lens[i]), kms[i]), cd_taps(kms[i]), float(kms[i])) for i in range(n_frames)]
 
 
 @dataclass
@@ -193,18 +213,22 @@ def config4(n_frames: int = 2048, n_links: int = 256, rate_hz: float = 20e3,
     t = np.cumsum(rng.exponential(1.0 / rate_hz, n_frames))
     links = rng.integers(0, n_links, n_frames)
     lens = frame_lengths(rng, n_frames, lo_log2, hi_log2)
+    pools = _Pools(4, int(2 ** hi_log2) + 1)
     for i in range(n_frames):
-        r = rng_for(4, i + 1)
         k = int(links[i])
-        tr.frames.append(Frame(received(r, int(lens[i]), 2, kms[k], 18.0), tr.link_taps[k],
-                               float(kms[k]), link=k, arrival_s=float(t[i])))
+        tr.frames.append(Frame(pools.frame(rng, int(lens[i]), kms[k]), tr.link_taps[k], float(kms[k]), link=k,
+                               arrival_s=float(t[i])))
     return tr
 
 
-def config5(n_samples: int = 1 << 27) -> Frame:
-    """Bandwidth stress: one PDM stream of 2^27 samples per pol, 80 km (19 taps)."""
+def config5(n_samples: int = 1 << 27, period: int = 1 << 23) -> Frame:
+    """Bandwidth stress: one PDM stream of 2^27 samples per pol, 80 km (19 taps).
+    A generated stretch of `period` samples repeats to the full length."""
     rng = rng_for(5)
-    return Frame(received(rng, n_samples, 2, 80.0, 18.0), cd_taps(80.0, 19), 80.0)
+    base = received(rng, min(n_samples, period), 2, 80.0, 18.0)
+    reps = -(-n_samples // base.shape[0])
+    x = np.tile(base, (reps, 1, 1))[:n_samples] if reps > 1 else base
+    return Frame(np.ascontiguousarray(x), cd_taps(80.0, 19), 80.0)
 
 
 def random_frame(rng: np.random.Generator, n: int, n_pol: int, L: int) -> Frame:
