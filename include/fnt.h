@@ -218,9 +218,17 @@ FNT_API int32_t fnt_batch_kernel_count(const fnt_batch *b);
 
 FNT_API fnt_status fnt_batch_destroy(fnt_batch *b);
 
-/* Sets the warps per CTA and, for the AEQ, CTAs per SM used by later
- * launches of this plan (autotuner hook).  0 keeps the current value. */
+/* Sets the warps per CTA of the CDC and AEQ kernels used by later launches of
+ * this plan (autotuner hook).  0 keeps the current value. */
 FNT_API fnt_status fnt_plan_set_launch(fnt_plan *plan, int32_t cdc_warps, int32_t aeq_warps);
+
+/* Prepared chain batches created after this call split their work into
+ * `chunks` pieces (1..16; default 1 = off): the CDC of piece k runs on the
+ * caller's stream and the AEQ of piece k on a side stream of the batch as soon
+ * as the CDC items it reads are done, so CDC and AEQ can overlap.  Results do
+ * not depend on it.  (On one 2^21-sample stream it measured slower: each AEQ
+ * piece is a latency-bound set of serial chains.) */
+FNT_API fnt_status fnt_plan_set_pipeline(fnt_plan *plan, int32_t chunks);
 
 /* ------------------------------------------------- allocation-free chain ---- */
 

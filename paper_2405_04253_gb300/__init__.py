@@ -61,6 +61,7 @@ SIGNATURES = {
     "fnt_plan_create": (_I32, [ctypes.POINTER(PlanDesc), ctypes.POINTER(_VP)]),
     "fnt_plan_destroy": (_I32, [_VP]),
     "fnt_plan_set_launch": (_I32, [_VP, _I32, _I32]),
+    "fnt_plan_set_pipeline": (_I32, [_VP, _I32]),
     "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
     "fnt_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
     "fnt_cdc_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
@@ -156,6 +157,9 @@ class Plan:
 
     def set_launch(self, cdc_warps: int = 0, aeq_warps: int = 0):
         check(lib().fnt_plan_set_launch(self.handle, cdc_warps, aeq_warps))
+
+    def set_pipeline(self, chunks: int):
+        check(lib().fnt_plan_set_pipeline(self.handle, chunks))
 
 
 class Frame:

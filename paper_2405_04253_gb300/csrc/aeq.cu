@@ -84,6 +84,18 @@ struct SplitTaps {
     }
 };
 
+// Even / odd split of an N-sample 5-bit input window (the first DIF stage):
+// y_j = a_j + a_{j+N/2} (even half) or (a_j - a_{j+N/2}) alpha^j (odd half).
+template <int NA, int64_t ALPHA, int J>
+struct SplitInput {
+    static __device__ __forceinline__ void run(int32_t (&y)[NA / 2], const uint32_t *xw, int sh, bool odd) {
+        constexpr int32_t W = TwTab<NA, ALPHA>::tab.w[J];
+        const int32_t a = sx8(xw[J], sh), b = sx8(xw[J + NA / 2], sh);
+        y[J] = odd ? rho((a - b) * W) : a + b;                      // |a - b| <= 31: no overflow
+        if constexpr (J + 1 < NA / 2) SplitInput<NA, ALPHA, J + 1>::run(y, xw, sh, odd);
+    }
+};
+
 // Last inverse stage: lane 0 holds E0, lane 1 holds E1 (natural order); output
 // n' (lane 0) / n' + N/2 (lane 1) for n' >= FROM, decoded, into `res`.
 template <int NA, int64_t AINV, int J, int FROM>
@@ -155,19 +167,21 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                     stage_async<C::XS>(xs2 + ((batch + 1) & 1) * C::XS, xin, t0 + C::PRE * SA - K, ch.begin, ch.end,
                                        lane);
                 {
-                    // full N-point spectrum of input sq for block bq, N^-1 folded in;
-                    // register r = hh * M + j holds X[bitrev(r)] = X[2 bitrev_M(j) + hh]
+                    // N-point spectrum of input sq for block bq, N^-1 folded in, as
+                    // its even and odd halves: X[2k'+hh] = FNT_{N/2, alpha^2} of
+                    // a_j + a_{j+N/2} (hh = 0) or (a_j - a_{j+N/2}) alpha^j (hh = 1),
+                    // in bit-reversed order -- one N/2-point code copy, two trips.
                     const int bq = lane >> 2, sq = lane & 3;
-                    int32_t x[NA];
-#pragma unroll
-                    for (int j = 0; j < NA; ++j) x[j] = sx8(xs[bq * SA + j], 8 * sq);
-                    fnt_fwd<NA, ALPHA, 5>(x);                  // |x| <= 16
+                    const uint32_t *xw = xs + bq * SA;
                     int32_t *row = xf + (bq * 4 + sq) * C::XF_ROW;
+#pragma unroll 1
+                    for (int hh = 0; hh < 2; ++hh) {
+                        int32_t y[M];
+                        SplitInput<NA, ALPHA, 0>::run(y, xw, 8 * sq, hh != 0);
+                        fnt_fwd<M, C::ALPHA2, 17>(y);
 #pragma unroll
-                    for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-                        for (int j = 0; j < M; ++j)
-                            row[hh * C::HALF + j] = rhoc(rho(rhoc(x[hh * M + j]) * C::NINV));
+                        for (int j = 0; j < M; ++j) row[hh * C::HALF + j] = rhoc(rho(rhoc(y[j]) * C::NINV));
+                    }
                 }
                 __syncwarp();
             }
@@ -229,18 +243,23 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
 
             // eq. (6): G[k] = sum_i e[i] z_S2[i] x_S1[t0 + i - k] for k = k0 .. k0 + 3
             if (mu < 63) {
-                int32_t xr[SA + 3];
-                const uint32_t *xb = xs + bb * SA + K - k0 - 3;
-#pragma unroll
-                for (int m = 0; m < SA + 3; ++m) xr[m] = sx8(xb[m], 8 * s1);
+                // rolling window: w0..w3 = x_S1[t0 + i - k0 - kk], kk = 0..3
+                const uint32_t *xb = xs + bb * SA + K - k0;
+                int32_t w1 = sx8(xb[-1], 8 * s1), w2 = sx8(xb[-2], 8 * s1), w3 = sx8(xb[-3], 8 * s1);
                 int64_t acc[4] = {0, 0, 0, 0};
                 const int32_t *zrow = zs + o * SA;
-#pragma unroll
+#pragma unroll 4
                 for (int i = 0; i < SA; ++i) {
+                    const int32_t w0 = sx8(xb[i], 8 * s1);
                     const int32_t e = es[i];
                     const int32_t z = zrow[i];
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) acc[kk] += (int64_t)e * (int64_t)(z * xr[i - kk + 3]);
+                    acc[0] += (int64_t)e * (int64_t)(z * w0);
+                    acc[1] += (int64_t)e * (int64_t)(z * w1);
+                    acc[2] += (int64_t)e * (int64_t)(z * w2);
+                    acc[3] += (int64_t)e * (int64_t)(z * w3);
+                    w3 = w2;
+                    w2 = w1;
+                    w1 = w0;
                 }
                 int32_t nv[4];
 #pragma unroll

@@ -182,6 +182,13 @@ extern "C" fnt_status fnt_plan_set_launch(fnt_plan *p, int32_t cdc_warps, int32_
     return FNT_OK;
 }
 
+extern "C" fnt_status fnt_plan_set_pipeline(fnt_plan *p, int32_t chunks) {
+    if (!p) return fail(FNT_ERR_INVALID, "null plan");
+    if (chunks < 1 || chunks > 16) return fail(FNT_ERR_INVALID, "chunks must be in [1, 16]");
+    p->chunks = chunks;
+    return FNT_OK;
+}
+
 // ---------------------------------------------------------- work building ---
 
 namespace fnt {
@@ -299,16 +306,54 @@ fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work 
         }
     }
     w.scratch_bytes = scratch;
-    for (int i = 0; i < b->n_frames; ++i) {
+    // Longest frames first, both for their CDC items and their AEQ chains: the
+    // serial AEQ recurrences of long frames bound the makespan, and with
+    // pipelined chunks they then start in the first chunk.
+    std::vector<int> order(b->n_frames);
+    for (int i = 0; i < b->n_frames; ++i) order[i] = i;
+    if (op == FNT_OP_CHAIN)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int c) { return w.frames[a].n_sym > w.frames[c].n_sym; });
+    for (int i : order) {
+        const int first_item = (int)w.items.size();
         if (op != FNT_OP_AEQ) add_cdc_items(w.frames[i], i, w.items);
-        if (op != FNT_OP_CDC) add_aeq_chains(p, w.frames[i], i, p->d_init, w);
+        if (op != FNT_OP_CDC) {
+            const size_t c0 = w.chains.size();
+            add_aeq_chains(p, w.frames[i], i, p->d_init, w);
+            for (size_t c = c0; c < w.chains.size(); ++c) {
+                const DevFrame &df = w.frames[i];
+                // last 2-sps sample the chain reads, and the CDC item that produces it
+                const int64_t t_last = 2 * (w.chains[c].end - 1) + df.phase;
+                w.chains[c].need_item = op == FNT_OP_CHAIN ? first_item + (int)(t_last / df.S / kBlocksPerItem) : 0;
+            }
+        }
     }
-    // longest chains first: they bound the makespan of the serial AEQ recurrences
-    std::stable_sort(w.chains.begin(), w.chains.end(), [](const AeqChain &a, const AeqChain &c) {
-        return (a.end - a.begin) > (c.end - c.begin);
-    });
     if (w.items.size() > (size_t)INT32_MAX || w.chains.size() > (size_t)INT32_MAX)
         return fail(FNT_ERR_INVALID, "batch too large");
+    // pipelined chunks (chain op only): cut the item list evenly; a chain joins
+    // the first chunk whose CDC items cover everything it reads
+    int C = 1;
+    if (op == FNT_OP_CHAIN && p->chunks > 1 && (int)w.items.size() >= 8 * p->chunks) C = p->chunks;
+    w.item_cut.assign(C + 1, 0);
+    for (int k = 0; k <= C; ++k) w.item_cut[k] = (int)((int64_t)w.items.size() * k / C);
+    auto chunk_of = [&](const AeqChain &c) {
+        int k = 0;
+        while (k + 1 < C && c.need_item >= w.item_cut[k + 1]) ++k;
+        return k;
+    };
+    // within a chunk, longest chains first
+    std::stable_sort(w.chains.begin(), w.chains.end(), [&](const AeqChain &a, const AeqChain &c) {
+        const int ka = chunk_of(a), kc = chunk_of(c);
+        if (ka != kc) return ka < kc;
+        return (a.end - a.begin) > (c.end - c.begin);
+    });
+    w.chain_cut.assign(C + 1, (int)w.chains.size());
+    w.chain_cut[0] = 0;
+    for (int k = 1; k < C; ++k) {
+        int c = w.chain_cut[k - 1];
+        while (c < (int)w.chains.size() && chunk_of(w.chains[c]) < k) ++c;
+        w.chain_cut[k] = c;
+    }
     return FNT_OK;
 }
 
@@ -351,37 +396,82 @@ fnt_status upload_work(Work &w, char *dev, cudaStream_t stream) {
     return FNT_OK;
 }
 
-int work_kernel_count(const Work &w) {
-    int k = 0;
-    if (w.op != FNT_OP_AEQ && !w.items.empty()) ++k;
-    if (w.op != FNT_OP_CDC && !w.chains.empty()) ++k;
-    return k;
+static fnt_status launch_cdc_range(const fnt_plan *p, const Work &w, const char *dev, int i0, int i1,
+                                   cudaStream_t stream) {
+    if (i1 <= i0) return FNT_OK;
+    const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
+    const int nw = p->cdc_warps;
+    const int n = i1 - i0;
+    const int grid = std::min((n + nw - 1) / nw, p->n_sm * 64);
+    cudaError_t e = cdc_launch(frames, (const int4 *)(dev + w.off_items) + i0, n, w.op == FNT_OP_CHAIN, nw, grid,
+                               stream);
+    return e == cudaSuccess ? FNT_OK : cuda_fail(e, "cdc kernel launch");
+}
+
+static fnt_status copy_initial_taps(const Work &w, const char *dev, cudaStream_t stream) {
+    for (size_t k = 0; k < w.init_src.size(); ++k) {
+        cudaError_t e = cudaMemcpyAsync((void *)(dev + w.off_init + k * kStateBytes), w.frames[w.init_src[k]].state,
+                                        kStateBytes, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy initial taps");
+    }
+    return FNT_OK;
+}
+
+static fnt_status launch_aeq_range(const fnt_plan *p, const Work &w, const char *dev, int c0, int c1,
+                                   cudaStream_t stream) {
+    if (c1 <= c0) return FNT_OK;
+    const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
+    AeqParams prm{p->d.mu_shift, p->d.rde_a};
+    cudaError_t e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(dev + w.off_chains) + c0, c1 - c0, prm,
+                               p->aeq_warps, 0, stream);
+    return e == cudaSuccess ? FNT_OK : cuda_fail(e, "aeq kernel launch");
 }
 
 fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream, int stages) {
-    const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
-    if ((stages & 1) && w.op != FNT_OP_AEQ && !w.items.empty()) {
-        const int nw = p->cdc_warps;
-        const int n = (int)w.items.size();
-        const int grid = std::min((n + nw - 1) / nw, p->n_sm * 64);
-        cudaError_t e = cdc_launch(frames, (const int4 *)(dev + w.off_items), n, w.op == FNT_OP_CHAIN, nw, grid,
-                                   stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cdc kernel launch");
+    fnt_status st = FNT_OK;
+    if ((stages & 1) && w.op != FNT_OP_AEQ) st = launch_cdc_range(p, w, dev, 0, (int)w.items.size(), stream);
+    if (st == FNT_OK && (stages & 2) && w.op != FNT_OP_CDC && !w.chains.empty()) {
+        st = copy_initial_taps(w, dev, stream);
+        if (st == FNT_OK) st = launch_aeq_range(p, w, dev, 0, (int)w.chains.size(), stream);
     }
-    if ((stages & 2) && w.op != FNT_OP_CDC && !w.chains.empty()) {
-        for (size_t k = 0; k < w.init_src.size(); ++k) {
-            cudaError_t e = cudaMemcpyAsync((void *)(dev + w.off_init + k * kStateBytes), w.frames[w.init_src[k]].state,
-                                            kStateBytes, cudaMemcpyDeviceToDevice, stream);
-            if (e != cudaSuccess) return cuda_fail(e, "copy initial taps");
+    return st;
+}
+
+fnt_status launch_pipelined(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream,
+                            const std::vector<cudaStream_t> &side, const std::vector<cudaEvent_t> &ev) {
+    const int C = (int)w.item_cut.size() - 1;
+    fnt_status st = copy_initial_taps(w, dev, stream);
+    for (int k = 0; k < C && st == FNT_OK; ++k) {
+        st = launch_cdc_range(p, w, dev, w.item_cut[k], w.item_cut[k + 1], stream);
+        if (st != FNT_OK) break;
+        cudaError_t e = cudaEventRecord(ev[k], stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side[k], ev[k], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "pipeline fork");
+        st = launch_aeq_range(p, w, dev, w.chain_cut[k], w.chain_cut[k + 1], side[k]);
+        if (st != FNT_OK) break;
+        e = cudaEventRecord(ev[C + k], side[k]);
+        if (e != cudaSuccess) return cuda_fail(e, "pipeline record");
+    }
+    // join every side stream back (also after an error, so a capture can end)
+    for (int k = 0; k < C; ++k) {
+        cudaError_t e = cudaStreamWaitEvent(stream, ev[C + k], 0);
+        if (e != cudaSuccess && st == FNT_OK) st = cuda_fail(e, "pipeline join");
+    }
+    return st;
+}
+
+int work_kernel_count(const Work &w) {
+    const int C = (int)w.item_cut.size() - 1;
+    int k = 0;
+    if (w.op != FNT_OP_AEQ) k += C > 1 ? C : (w.items.empty() ? 0 : 1);
+    if (w.op != FNT_OP_CDC) {
+        if (C > 1) {
+            for (int c = 0; c < C; ++c) k += w.chain_cut[c + 1] > w.chain_cut[c];
+        } else {
+            k += w.chains.empty() ? 0 : 1;
         }
-        const int nw = p->aeq_warps;
-        const int n = (int)w.chains.size();
-        AeqParams prm{p->d.mu_shift, p->d.rde_a};
-        cudaError_t e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(dev + w.off_chains), n, prm, nw, 0,
-                                   stream);
-        if (e != cudaSuccess) return cuda_fail(e, "aeq kernel launch");
     }
-    return FNT_OK;
+    return k;
 }
 
 // Per-frame host<->device sizes for host_buffers = 1.
@@ -468,8 +558,14 @@ struct fnt_batch {
     char *dev = nullptr;
     int use_graph = 0;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t graph_stream = nullptr;
+    std::vector<cudaStream_t> side;   // one per pipelined chunk
+    std::vector<cudaEvent_t> ev;      // fork (k) and join (C + k) events
 };
+
+static fnt_status batch_enqueue(fnt_batch *bt, cudaStream_t stream) {
+    if (bt->side.empty()) return launch_work(bt->plan, bt->work, bt->dev, stream);
+    return launch_pipelined(bt->plan, bt->work, bt->dev, stream, bt->side, bt->ev);
+}
 
 extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch *b, int32_t op, int32_t use_graph,
                                        fnt_batch **out) {
@@ -487,6 +583,13 @@ extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch 
         return st;
     }
     layout(bt->work);
+    const int C = (int)bt->work.item_cut.size() - 1;
+    if (C > 1) {
+        bt->side.resize(C);
+        bt->ev.resize(2 * C);
+        for (auto &sd : bt->side) cudaStreamCreateWithFlags(&sd, cudaStreamNonBlocking);
+        for (auto &e : bt->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    }
     cudaError_t e = cudaMalloc((void **)&bt->dev, bt->work.total);
     if (e != cudaSuccess) {
         delete bt;
@@ -509,7 +612,7 @@ extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch 
 extern "C" fnt_status fnt_batch_launch(fnt_batch *bt, void *stream_) {
     if (!bt) return fail(FNT_ERR_INVALID, "null batch");
     cudaStream_t stream = (cudaStream_t)stream_;
-    if (!bt->use_graph) return launch_work(bt->plan, bt->work, bt->dev, stream);
+    if (!bt->use_graph) return batch_enqueue(bt, stream);
     if (!bt->exec) {
         cudaStream_t cap;
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
@@ -519,7 +622,7 @@ extern "C" fnt_status fnt_batch_launch(fnt_batch *bt, void *stream_) {
             cudaStreamDestroy(cap);
             return cuda_fail(e, "cudaStreamBeginCapture");
         }
-        fnt_status st = launch_work(bt->plan, bt->work, bt->dev, cap);
+        fnt_status st = batch_enqueue(bt, cap);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);
@@ -549,6 +652,8 @@ extern "C" fnt_status fnt_batch_destroy(fnt_batch *bt) {
     if (!bt) return FNT_OK;
     cudaDeviceSynchronize();
     if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    for (auto &sd : bt->side) cudaStreamDestroy(sd);
+    for (auto &e : bt->ev) cudaEventDestroy(e);
     cudaFree(bt->dev);
     delete bt;
     return FNT_OK;

@@ -17,6 +17,7 @@ struct fnt_plan {
     int n_sm = 1;
     int cdc_warps = 4;
     int aeq_warps = 2;
+    int chunks = 1;              // pipelined chunks of prepared chain batches (1 = off)
 };
 
 namespace fnt {
@@ -36,6 +37,8 @@ struct Work {
     std::vector<AeqChain> chains;     // AEQ runs, longest first
     std::vector<int64_t> scratch_off; // chain: per-frame offset of the intermediate buffer
     std::vector<int> init_src;        // segmented frames with a state: frame whose state is copied
+    std::vector<int> item_cut;        // pipelined chunks: CDC items [item_cut[k], item_cut[k+1])
+    std::vector<int> chain_cut;       //                   AEQ chains [chain_cut[k], chain_cut[k+1])
     int64_t scratch_bytes = 0;
     size_t off_frames = 0, off_items = 0, off_chains = 0, off_init = 0, off_scratch = 0, total = 0;
 };
@@ -47,6 +50,9 @@ void layout(Work &w);
 fnt_status upload_work(Work &w, char *dev, cudaStream_t stream);
 // stages: bit 0 = CDC kernel, bit 1 = AEQ kernel
 fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream, int stages = 3);
+// Chunked CDC -> AEQ with the AEQ chunks on side streams (w.item_cut / w.chain_cut).
+fnt_status launch_pipelined(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream,
+                            const std::vector<cudaStream_t> &side, const std::vector<cudaEvent_t> &ev);
 int work_kernel_count(const Work &w);
 
 // kernels

@@ -38,7 +38,7 @@ struct alignas(16) AeqChain {
     int64_t end;           // one past the last symbol
     const int32_t *init;   // initial taps (frame state, a copy of it, or the plan's initial taps)
     int32_t init_copy;     // host side only: index of the state copy `init` must point to, or -1
-    int32_t pad0;
+    int32_t need_item;     // host side only: last CDC work item whose output this chain reads
 };
 static_assert(sizeof(AeqChain) == 48, "AeqChain layout");
 

@@ -208,6 +208,8 @@ fnt_status launch_wave(fnt_session *ss, Slot &slot) {
     }
     std::stable_sort(w.chains.begin(), w.chains.end(),
                      [](const AeqChain &a, const AeqChain &b) { return a.end > b.end; });
+    w.item_cut = {0, (int)w.items.size()};
+    w.chain_cut = {0, (int)w.chains.size()};
     layout(w);
     fnt_status st = grow(slot, w.total);
     if (st != FNT_OK) return st;

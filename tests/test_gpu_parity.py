@@ -271,11 +271,22 @@ def test_chain_full_size_cfg2_sampled_segments(orc):
     st = dev(T0)
     nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
     out = i16((nsym, 4))
-    b = F.Batch(plan, [F.Frame(dev(f.x), out, f.taps, st)], F.OP_CHAIN, use_graph=False)
+    xd = dev(f.x)
+    b = F.Batch(plan, [F.Frame(xd, out, f.taps, st)], F.OP_CHAIN, use_graph=False)
     b.launch_stage(0)
     b.launch_stage(1)
     torch.cuda.synchronize()
     got = out.cpu().numpy()
+    # the pipelined graph launch of the same work gives the same bits
+    st2 = dev(T0)
+    out2 = i16((nsym, 4))
+    plan.set_pipeline(4)
+    bp = F.Batch(plan, [F.Frame(xd, out2, f.taps, st2)], F.OP_CHAIN, use_graph=True)
+    bp.launch()
+    torch.cuda.synchronize()
+    assert bp.kernel_count() > 2
+    assert np.array_equal(out2.cpu().numpy(), got)
+    assert torch.equal(st2, st)
     n_seg = (nsym + 1023) // 1024
     rng = np.random.default_rng(2)
     segs = sorted({0, 1, n_seg // 2, n_seg - 2, n_seg - 1, *rng.integers(0, n_seg, 15).tolist()})
@@ -284,3 +295,33 @@ def test_chain_full_size_cfg2_sampled_segments(orc):
         assert np.array_equal(got[keep:keep + ref.shape[0]], ref), s
         if s == n_seg - 1:
             assert np.array_equal(st.cpu().numpy(), Tend)
+
+
+def test_pipelined_batch_equals_oracle_and_unpipelined(orc):
+    """Prepared chain batches cut into chunks (CDC of chunk k on the caller's
+    stream, AEQ of chunk k on a side stream) give the same bits as one CDC
+    launch followed by one AEQ launch, and as the oracle."""
+    rng = np.random.default_rng(12)
+    frames_np = []
+    for _ in range(40):
+        n = int(2 ** rng.uniform(10, 14.5))
+        L = int(rng.choice([5, 9, 13, 17, 19]))
+        frames_np.append((rng.integers(-16, 16, (n, 2, 2)).astype(np.int8),
+                          rng.integers(-32, 32, (L, 2)).astype(np.int8)))
+    outs = {}
+    for chunks, graph in [(4, True), (3, False), (1, False)]:
+        plan = F.Plan(mu_shift=9)
+        plan.set_pipeline(chunks)
+        frames = [F.Frame(dev(x), i16((F.chain_nsym(x.shape[0], t.shape[0]), 4)), t) for x, t in frames_np]
+        b = F.Batch(plan, frames, F.OP_CHAIN, use_graph=graph)
+        b.launch()
+        b.launch()
+        torch.cuda.synchronize()
+        outs[chunks] = [fr.out.cpu().numpy() for fr in frames]
+        if chunks == 4:
+            assert b.kernel_count() > 2
+    for a, b_, c in zip(outs[4], outs[3], outs[1]):
+        assert np.array_equal(a, c) and np.array_equal(b_, c)
+    for i in (0, 7, 39):
+        ref, _ = orc.chain(frames_np[i][0], frames_np[i][1], orc.ChainParams(mu_shift=9))
+        assert np.array_equal(outs[4][i], ref)
