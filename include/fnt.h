@@ -245,7 +245,7 @@ FNT_API fnt_status fnt_plan_set_pipeline(fnt_plan *plan, int32_t chunks);
  *
  * The caller passes the frame as for fnt_cdc_aeq_run (device in / out / state,
  * host taps).  The work tables and the intermediate CDC -> AEQ symbols live in
- * a fixed array of about 4.2 MiB in device memory that belongs to the library
+ * a fixed array of about 4.3 MiB in device memory that belongs to the library
  * image: every GPU that loads libfnt holds it until the process exits.  The
  * first call on a device, with that device current, looks up the array's
  * address; make that first call before any stream capture.  All calls on a

@@ -62,6 +62,13 @@ __device__ __forceinline__ void cp_async4(uint32_t *smem, const uint32_t *gmem, 
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// (int64) a * b + c with one wide multiply-add.
+__device__ __forceinline__ int64_t mad_wide(int32_t a, int32_t b, int64_t c) {
+    int64_t d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
 // dst[q] = x[t_first + q] for q < WORDS, zero outside [lo, hi), issued asynchronously.
 template <int WORDS>
 __device__ __forceinline__ void stage_async(uint32_t *dst, const uint32_t *x, int64_t t_first, int64_t lo, int64_t hi,
@@ -243,20 +250,22 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
 
             // eq. (6): G[k] = sum_i e[i] z_S2[i] x_S1[t0 + i - k] for k = k0 .. k0 + 3
             if (mu < 63) {
-                // rolling window: w0..w3 = x_S1[t0 + i - k0 - kk], kk = 0..3
-                const uint32_t *xb = xs + bb * SA + K - k0;
-                int32_t w1 = sx8(xb[-1], 8 * s1), w2 = sx8(xb[-2], 8 * s1), w3 = sx8(xb[-3], 8 * s1);
+                // rolling window: w0..w3 = x_S1[t0 + i - k0 - kk], kk = 0..3, read
+                // as sign-extending byte loads of stream s1 from the staged words
+                const int8_t *xb = (const int8_t *)(xs + bb * SA + K - k0) + s1;
+                int32_t w1 = xb[-4], w2 = xb[-8], w3 = xb[-12];
                 int64_t acc[4] = {0, 0, 0, 0};
                 const int32_t *zrow = zs + o * SA;
 #pragma unroll 4
                 for (int i = 0; i < SA; ++i) {
-                    const int32_t w0 = sx8(xb[i], 8 * s1);
+                    const int32_t w0 = xb[4 * i];
                     const int32_t e = es[i];
                     const int32_t z = zrow[i];
-                    acc[0] += (int64_t)e * (int64_t)(z * w0);
-                    acc[1] += (int64_t)e * (int64_t)(z * w1);
-                    acc[2] += (int64_t)e * (int64_t)(z * w2);
-                    acc[3] += (int64_t)e * (int64_t)(z * w3);
+                    // |z w| <= 2^19: 32-bit product; e (z w) + acc in one wide multiply-add
+                    acc[0] = mad_wide(e, z * w0, acc[0]);
+                    acc[1] = mad_wide(e, z * w1, acc[1]);
+                    acc[2] = mad_wide(e, z * w2, acc[2]);
+                    acc[3] = mad_wide(e, z * w3, acc[3]);
                     w3 = w2;
                     w2 = w1;
                     w1 = w0;

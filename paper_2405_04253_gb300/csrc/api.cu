@@ -248,7 +248,8 @@ static fnt_status make_frame(const fnt_plan *p, const fnt_frame &f, int op, int 
 static void add_cdc_items(const DevFrame &df, int fi, std::vector<int4> &items) {
     const int64_t nblk = (df.n + df.S - 1) / df.S;
     for (int64_t b = 0; b < nblk; b += kBlocksPerItem)
-        items.push_back(make_int4(fi, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), 0));
+        for (int p = 0; p < df.n_pol; ++p)
+            items.push_back(make_int4(fi, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), p));
 }
 
 // AEQ runs of one frame.  Unsegmented: one chain that reads and writes the
@@ -324,7 +325,8 @@ fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work 
                 const DevFrame &df = w.frames[i];
                 // last 2-sps sample the chain reads, and the CDC item that produces it
                 const int64_t t_last = 2 * (w.chains[c].end - 1) + df.phase;
-                w.chains[c].need_item = op == FNT_OP_CHAIN ? first_item + (int)(t_last / df.S / kBlocksPerItem) : 0;
+                w.chains[c].need_item =
+                    op == FNT_OP_CHAIN ? first_item + (int)(t_last / df.S / kBlocksPerItem) * df.n_pol + df.n_pol - 1 : 0;
             }
         }
     }

@@ -2,8 +2,8 @@
 // Fermat number transforms over Z_65537 with radix sqrt(2) = 4080 (section
 // "Proposed FNT-CDC&AEQ structure"; eqs. (1), (2), (5), (7), (8)).
 //
-// Work item = 32 consecutive overlap-save blocks of one frame, one warp; lane l
-// owns block b0 + l entirely in registers:
+// Work item = 32 consecutive overlap-save blocks of one polarisation of a frame,
+// one warp; lane l owns block b0 + l entirely in registers:
 //   u = x_re + 2^8 x_im, v = x_re - 2^8 x_im          (2^8 = sqrt(-1) mod F)
 //   P = FNT(u) . H_u,   Q = FNT(v) . H_v                (H = FNT of the taps,
 //                                                        times N^-1 2^-1)
@@ -91,7 +91,7 @@ __device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, cons
 }
 
 template <bool CHAIN>
-__global__ void __launch_bounds__(128, 2) cdc_kernel(const DevFrame *__restrict__ frames,
+__global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict__ frames,
                                                      const int4 *__restrict__ items, int n_items) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int32_t s_pow[kN];
@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(128, 2) cdc_kernel(const DevFrame *__restrict_
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    uint32_t *win = smem + warp * kWarpWords;     // [64][33] input words; pol-1 results
-    uint32_t *o0 = win + kN * kRow;               // [64][33] pol-0 results
+    uint32_t *win = smem + warp * kWarpWords;     // [64][33] input words (both polarisations)
+    uint32_t *o0 = win + kN * kRow;               // [64][33] results of the item's polarisation
     int32_t *hs = (int32_t *)(o0 + kN * kRow);    // H_u [64], H_v [64] in bit-reversed order
 
     for (int it = blockIdx.x * wpb + warp; it < n_items; it += gridDim.x * wpb) {
@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(128, 2) cdc_kernel(const DevFrame *__restrict_
         const DevFrame &fr = frames[item.x];
         const int64_t b0 = item.y;
         const int nb = item.z;
+        const int pol = item.w;                       // polarisation this warp computes
         const int S = fr.S;
         const int L = fr.L;
         const int npol = fr.n_pol;
@@ -166,11 +167,7 @@ __global__ void __launch_bounds__(128, 2) cdc_kernel(const DevFrame *__restrict_
         }
         __syncwarp();
 
-#pragma unroll 1
-        for (int pol = 0; pol < npol; ++pol) {
-            // pol 0 results go to o0; pol 1 results overwrite the lane's own window column
-            cdc_block(win, pol ? win : o0, hs, lane, 16 * pol);
-        }
+        cdc_block(win, o0, hs, lane, 16 * pol);
         __syncwarp();
 
         if (!CHAIN) {
@@ -182,11 +179,7 @@ __global__ void __launch_bounds__(128, 2) cdc_kernel(const DevFrame *__restrict_
                     const int64_t t = (b0 + l) * S + jj;
                     if (jj < S && t < n) {
                         const int pos = (kN - S + jj) * kRow + l;
-                        if (npol == 2) {
-                            *(uint2 *)(out + t * 4) = make_uint2(o0[pos], win[pos]);
-                        } else {
-                            *(uint32_t *)(out + t * 2) = o0[pos];
-                        }
+                        *(uint32_t *)(out + (t * npol + pol) * 2) = o0[pos];
                     }
                 }
             }
@@ -194,20 +187,18 @@ __global__ void __launch_bounds__(128, 2) cdc_kernel(const DevFrame *__restrict_
             // requantise to 5 bits and keep times t = phase (mod 2)
             const int sft = fr.shift;
             const int32_t rnd = sft > 0 ? (1 << (sft - 1)) : 0;
-            uint32_t *xa = (uint32_t *)fr.aeq_in;
+            uint16_t *xa = (uint16_t *)fr.aeq_in;
             for (int l = 0; l < nb; ++l) {
                 const int64_t t0 = (b0 + l) * S;
                 const int jj = (int)((t0 - fr.phase) & 1) + 2 * lane;
                 const int64_t t = t0 + jj;
                 if (jj < S && t < n) {
                     const int pos = (kN - S + jj) * kRow + l;
-                    const uint32_t w0 = o0[pos], w1 = win[pos];
+                    const uint32_t w0 = o0[pos];
                     const int32_t c0 = sat5(((int32_t)(int16_t)(w0 & 0xFFFF) + rnd) >> sft);
                     const int32_t c1 = sat5((((int32_t)w0 >> 16) + rnd) >> sft);
-                    const int32_t c2 = sat5(((int32_t)(int16_t)(w1 & 0xFFFF) + rnd) >> sft);
-                    const int32_t c3 = sat5((((int32_t)w1 >> 16) + rnd) >> sft);
-                    xa[(t - fr.phase) >> 1] = (uint32_t)(c0 & 0xFF) | ((uint32_t)(c1 & 0xFF) << 8) |
-                                              ((uint32_t)(c2 & 0xFF) << 16) | ((uint32_t)c3 << 24);
+                    // this polarisation's two bytes (I, Q) of the symbol's 4-byte word
+                    xa[2 * ((t - fr.phase) >> 1) + pol] = (uint16_t)((c0 & 0xFF) | ((c1 & 0xFF) << 8));
                 }
             }
         }

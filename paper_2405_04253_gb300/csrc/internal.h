@@ -10,6 +10,8 @@ constexpr int kCdcN = 64;          // CDC transform length
 constexpr int kMaxCdTaps = 31;     // |Re z|, |Im z| <= 31 * 2 * 16 * 32 < 2^15 (eq. (5), int16 out)
 constexpr int kAeqK = 16;          // taps per real AEQ filter
 constexpr int kBlocksPerItem = 32; // CDC blocks per warp work item (one per lane)
+// CDC work item: int4 (frame, first block, blocks, polarisation); a group of 32
+// blocks of an n_pol = 2 frame is two consecutive items (pol 0, pol 1).
 
 // One frame as the kernels see it (128 bytes, 16-byte aligned).
 struct alignas(16) DevFrame {

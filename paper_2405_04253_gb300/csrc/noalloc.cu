@@ -33,7 +33,7 @@ namespace {
 
 constexpr int64_t kMaxSamples = FNT_NOALLOC_MAX_SAMPLES;
 constexpr int64_t kMaxSym = kMaxSamples / 2;
-constexpr int kMaxItems = (int)((kMaxSamples / 32 + kBlocksPerItem - 1) / kBlocksPerItem);   // step S >= 32
+constexpr int kMaxItems = 2 * (int)((kMaxSamples / 32 + kBlocksPerItem - 1) / kBlocksPerItem);   // S >= 32, 2 pols
 constexpr int kMaxChains = FNT_NOALLOC_MAX_SEGMENTS;
 
 constexpr size_t kOffFrame = 0;
@@ -125,7 +125,8 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
     const int64_t nblk = (f->n + S - 1) / S;
     int n_items = 0;
     for (int64_t b = 0; b < nblk; b += kBlocksPerItem)
-        g_items[n_items++] = make_int4(0, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), 0);
+        for (int pol = 0; pol < 2; ++pol)
+            g_items[n_items++] = make_int4(0, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), pol);
 
     int nc = 0;
     if (n_chains == 1) {

@@ -193,7 +193,8 @@ fnt_status launch_wave(fnt_session *ss, Slot &slot) {
         memcpy(df.taps, lk.taps, sizeof df.taps);
         const int64_t nblk = (r.n + lk.S - 1) / lk.S;
         for (int64_t b = 0; b < nblk; b += kBlocksPerItem)
-            w.items.push_back(make_int4(i, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), 0));
+            for (int pol = 0; pol < 2; ++pol)
+                w.items.push_back(make_int4(i, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), pol));
         if (r.n_sym > 0) {
             AeqChain c{};
             c.frame = i;

@@ -261,12 +261,12 @@ def test_chain_host_buffers_equal_device(orc):
 
 def test_chain_full_size_cfg2_sampled_segments(orc):
     """The benchmark's workload at full size (2^21 samples per polarisation,
-    segments of 1024 + 128, carried state), launched as bench.py launches it;
+    segments of 1024 + 48, carried state), launched as bench.py launches it;
     sampled segments recomputed one by one by the oracle."""
     f = synth.config2()
     assert f.x.shape == (1 << 21, 2, 2)
-    plan = F.Plan(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=1024, aeq_warmup=128)
-    prm = orc.ChainParams(n_aeq=64, alpha_aeq=4080, mu_shift=9, seg_len=1024, warmup=128)
+    plan = F.Plan(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=1024, aeq_warmup=48)
+    prm = orc.ChainParams(n_aeq=64, alpha_aeq=4080, mu_shift=9, seg_len=1024, warmup=48)
     T0 = orc.aeq_init_taps(16, 2048)
     st = dev(T0)
     nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
