@@ -117,6 +117,25 @@ typedef struct fnt_plan fnt_plan;
 FNT_API fnt_status fnt_plan_create(const fnt_plan_desc *desc, fnt_plan **out);
 FNT_API fnt_status fnt_plan_destroy(fnt_plan *plan);
 
+/* Multiplication counts of the kernels for a plan description (no device
+ * needed), in the units of Tab. 1
+ * (real multiplications per symbol; twiddle products by powers of the radix
+ * are not counted, as in the paper, since they are shifts in its hardware).
+ *   cdc_mults_per_symbol  pointwise products of the CDC per symbol and
+ *                         polarisation, for a frame with cd_len taps
+ *                         (2 N per block, S / 2 symbols per block at 2 sps)
+ *   aeq_mults_per_symbol  pointwise products of the 4x4 AEQ per symbol
+ *                         (32 N_aeq per block of N_aeq - 16 symbols)
+ * At the operating point of Tab. 1 (CDC N = 64 with 50 % overlap, i.e.
+ * cdc_step = 32; AEQ N = 32) these are 8 and 64. */
+typedef struct fnt_op_counts {
+    double cdc_mults_per_symbol;
+    double aeq_mults_per_symbol;
+    double cdc_butterflies_per_symbol;
+} fnt_op_counts;
+
+FNT_API fnt_status fnt_op_counts_for(const fnt_plan_desc *desc, int32_t cd_len, fnt_op_counts *out);
+
 /* ---------------------------------------------------------------- frames ---- */
 
 /*
@@ -264,10 +283,13 @@ FNT_API fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *plan, const fnt_frame
  * and an AEQ tap state that stays in device memory and carries from one of the
  * link's frames to the next (frames of a link run in submission order; the
  * delay line does not carry).  Requests are admitted while the session's device
- * memory (inputs, outputs, intermediate buffers and work lists of admitted
- * requests) stays within mem_cap_bytes; the scheduler packs ready frames of
+ * memory for them (intermediate CDC -> AEQ symbols, state copies) stays within
+ * mem_cap_bytes; the scheduler packs ready frames of
  * idle links into waves and runs up to n_streams waves at once, so requests
- * admitted while others run overlap with them on the device.
+ * admitted while others run overlap with them on the device.  A plan with AEQ
+ * segments cuts a long frame into segments that start from the link's taps as
+ * the frame began (as fnt_cdc_aeq_run does with a frame state); the last
+ * segment writes the link's taps.
  */
 typedef struct fnt_session fnt_session;
 
@@ -289,9 +311,9 @@ FNT_API fnt_status fnt_session_create(const fnt_plan *plan, int32_t n_links, siz
 FNT_API fnt_status fnt_session_set_link(fnt_session *s, int32_t link, const int8_t *cd_taps, int32_t L);
 
 /* Submits one PDM frame: in = int8 [n][2][2], out = int16 [n_sym][4] (as for
- * fnt_cdc_aeq_run).  Both are either device pointers or page-locked host
- * pointers (the session copies through its own device memory); pageable host
- * memory is rejected with FNT_ERR_INVALID.  The buffers must stay valid until
+ * fnt_cdc_aeq_run).  Each is device memory or page-locked host memory, which
+ * the kernels read and write in place through its device mapping (no staging
+ * copies); pageable host memory is rejected with FNT_ERR_INVALID.  The buffers must stay valid until
  * the request completes.  Returns FNT_ERR_BUSY, admitting nothing, when the
  * request does not fit under the memory cap right now. */
 FNT_API fnt_status fnt_session_submit(fnt_session *s, int32_t link, const void *in, int64_t n, void *out,

@@ -46,6 +46,11 @@ class BatchC(ctypes.Structure):
                 ("frames", ctypes.POINTER(FrameC))]
 
 
+class OpCounts(ctypes.Structure):
+    _fields_ = [("cdc_mults_per_symbol", ctypes.c_double), ("aeq_mults_per_symbol", ctypes.c_double),
+                ("cdc_butterflies_per_symbol", ctypes.c_double)]
+
+
 class Completion(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("link", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("n_sym", ctypes.c_int64), ("submit_us", ctypes.c_double), ("start_us", ctypes.c_double),
@@ -62,6 +67,7 @@ SIGNATURES = {
     "fnt_plan_destroy": (_I32, [_VP]),
     "fnt_plan_set_launch": (_I32, [_VP, _I32, _I32]),
     "fnt_plan_set_pipeline": (_I32, [_VP, _I32]),
+    "fnt_op_counts_for": (_I32, [ctypes.POINTER(PlanDesc), _I32, ctypes.POINTER(OpCounts)]),
     "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
     "fnt_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
     "fnt_cdc_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
@@ -133,6 +139,14 @@ def default_desc(**over) -> PlanDesc:
     for k, v in over.items():
         setattr(d, k, v)
     return d
+
+
+def op_counts(cd_len: int, **over) -> dict:
+    """Tab. 1 multiplication counts of the kernels for a plan description."""
+    d = default_desc(**over)
+    oc = OpCounts()
+    check(lib().fnt_op_counts_for(ctypes.byref(d), cd_len, ctypes.byref(oc)))
+    return {f: getattr(oc, f) for f, _ in OpCounts._fields_}
 
 
 class Plan:

@@ -306,6 +306,10 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
 
 }  // namespace
 
+// Pointwise products mod F per AEQ block of both polarisations: 16 filters x 2
+// tap groups x N (each split over two lanes as two N/2 halves).
+int aeq_mults_per_block(int na) { return 32 * na; }
+
 size_t aeq_smem_bytes(int na, int warps) {
     return (size_t)warps * (na == 64 ? AeqCfg<64, 4080>::WORDS : AeqCfg<32, 2>::WORDS) * sizeof(uint32_t);
 }

@@ -182,6 +182,20 @@ extern "C" fnt_status fnt_plan_set_launch(fnt_plan *p, int32_t cdc_warps, int32_
     return FNT_OK;
 }
 
+extern "C" fnt_status fnt_op_counts_for(const fnt_plan_desc *d, int32_t cd_len, fnt_op_counts *out) {
+    if (!d || !out) return fail(FNT_ERR_INVALID, "null argument");
+    if (cd_len < 1 || cd_len > kMaxCdTaps) return fail(FNT_ERR_BOUND, "cd_len %d outside 1..%d", cd_len, kMaxCdTaps);
+    if (d->n_cdc != kCdcN || (d->n_aeq != 32 && d->n_aeq != 64) || d->aeq_taps != kAeqK)
+        return fail(FNT_ERR_INVALID, "unsupported transform lengths");
+    const int S = d->cdc_step ? d->cdc_step : kCdcN - cd_len + 1;
+    if (S < 32 || S > kCdcN - cd_len + 1) return fail(FNT_ERR_BOUND, "step %d with %d taps", S, cd_len);
+    const double sym_per_block = S / 2.0;                  // 2 samples per symbol
+    out->cdc_mults_per_symbol = cdc_mults_per_block() / sym_per_block;
+    out->cdc_butterflies_per_symbol = cdc_butterflies_per_block() / sym_per_block;
+    out->aeq_mults_per_symbol = (double)aeq_mults_per_block(d->n_aeq) / (d->n_aeq - kAeqK);
+    return FNT_OK;
+}
+
 extern "C" fnt_status fnt_plan_set_pipeline(fnt_plan *p, int32_t chunks) {
     if (!p) return fail(FNT_ERR_INVALID, "null plan");
     if (chunks < 1 || chunks > 16) return fail(FNT_ERR_INVALID, "chunks must be in [1, 16]");

@@ -210,6 +210,11 @@ __global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict_
 
 size_t cdc_smem_bytes(int warps) { return (size_t)warps * kWarpWords * sizeof(uint32_t); }
 
+// Pointwise products mod F that cdc_block performs per overlap-save block and
+// polarisation (P = FNT(u) H_u and Q = FNT(v) H_v), and its transform butterflies.
+int cdc_mults_per_block() { return 2 * kN; }
+int cdc_butterflies_per_block() { return 4 * (kN / 2) * 6; }
+
 cudaError_t cdc_configure() {
     const size_t max_smem = cdc_smem_bytes(8);
     cudaError_t e = cudaFuncSetAttribute(cdc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -57,6 +57,9 @@ int work_kernel_count(const Work &w);
 
 // kernels
 size_t cdc_smem_bytes(int warps);
+int cdc_mults_per_block();
+int cdc_butterflies_per_block();
+int aeq_mults_per_block(int na);
 cudaError_t cdc_configure();
 cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, int warps, int grid,
                        cudaStream_t stream);

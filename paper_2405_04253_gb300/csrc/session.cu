@@ -3,14 +3,17 @@
 // Each link has fixed CD taps and an AEQ tap state that lives in device memory
 // and carries across the link's frames.  Requests are admitted while the
 // session's device arena (capped at mem_cap bytes) can hold their buffers:
-// intermediate CDC->AEQ symbols and, for page-locked host requests, device
-// copies of input and output.  A scheduler packs the oldest ready frame of each
+// intermediate CDC->AEQ symbols (and, for segmented frames, a copy of the link's
+// taps).  Inputs and outputs stay where the caller put them: device memory, or
+// page-locked host memory that the kernels read and write directly.  A scheduler packs the oldest ready frame of each
 // idle link into a wave, runs the CDC and AEQ kernels for the whole wave on one
 // of n_streams streams, and records an event; up to n_streams waves run at
 // once, so requests admitted while others are on the GPU overlap with them.  A
 // link is idle while none of its frames is in flight, which keeps every link's
 // frames in submission order (its tap state is read and written by one chain at
-// a time).  Completion is observed on the host by querying the wave's event.
+// a time).  With AEQ segments in the plan, a long frame's segments start from the
+// link's taps as the frame began and run in parallel; the last one writes the
+// link's taps.  Completion is observed on the host by querying the wave's event.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -84,13 +87,12 @@ class Arena {
 struct Request {
     uint64_t ticket = 0;
     int link = 0;
-    const int8_t *in = nullptr;   // caller pointer
-    void *out = nullptr;          // caller pointer
-    bool host_io = false;
+    const int8_t *in = nullptr;   // device-accessible input (device memory, or the device
+    void *out = nullptr;          // mapping of page-locked host memory) and output
     int64_t n = 0;
     int64_t n_sym = 0;
     size_t off = 0, bytes = 0;    // arena reservation
-    size_t off_in = 0, off_out = 0, off_scratch = 0;
+    size_t off_scratch = 0, off_init = 0;
     double submit_us = 0, start_us = 0;
 };
 
@@ -141,9 +143,23 @@ namespace {
 
 constexpr int kMaxWave = 1024;
 
-size_t request_bytes(const Request &r) {
+// One launch copies the taps of every segmented frame of a wave (link state ->
+// the frame's copy), instead of one API copy per frame.
+struct StateCopy {
+    const int32_t *src;
+    int32_t *dst;
+};
+
+__global__ void copy_states(const StateCopy *__restrict__ cp, int n) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x)
+        for (int t = threadIdx.x; t < 16 * kAeqK; t += blockDim.x) cp[i].dst[t] = cp[i].src[t];
+}
+
+bool segmented(const fnt_plan *p, int64_t n_sym) { return p->d.aeq_segment > 0 && n_sym > p->d.aeq_segment; }
+
+size_t request_bytes(const fnt_plan *p, const Request &r) {
     size_t b = up256((size_t)r.n_sym * 4);                 // AEQ input symbols
-    if (r.host_io) b += up256((size_t)r.n * 4) + up256((size_t)r.n_sym * 8);
+    if (segmented(p, r.n_sym)) b += up256(kStateBytes);   // the link's taps as the frame began
     return b;
 }
 
@@ -179,8 +195,8 @@ fnt_status launch_wave(fnt_session *ss, Slot &slot) {
         const LinkState &lk = ss->links[r.link];
         DevFrame &df = w.frames[i];
         memset(&df, 0, sizeof df);
-        df.in = r.host_io ? (const int8_t *)(ss->arena_mem + r.off_in) : r.in;
-        df.out = r.host_io ? (void *)(ss->arena_mem + r.off_out) : r.out;
+        df.in = r.in;
+        df.out = r.out;
         df.aeq_in = (int8_t *)(ss->arena_mem + r.off_scratch);
         df.state = ss->d_state + (size_t)r.link * 16 * kAeqK;
         df.n = r.n;
@@ -195,7 +211,7 @@ fnt_status launch_wave(fnt_session *ss, Slot &slot) {
         for (int64_t b = 0; b < nblk; b += kBlocksPerItem)
             for (int pol = 0; pol < 2; ++pol)
                 w.items.push_back(make_int4(i, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), pol));
-        if (r.n_sym > 0) {
+        if (r.n_sym > 0 && !segmented(ss->plan, r.n_sym)) {
             AeqChain c{};
             c.frame = i;
             c.write_state = 1;
@@ -205,6 +221,21 @@ fnt_status launch_wave(fnt_session *ss, Slot &slot) {
             c.init = df.state;
             c.init_copy = -1;
             w.chains.push_back(c);
+        } else if (r.n_sym > 0) {
+            // segments start from the link's taps as the frame began (copied below);
+            // the last one writes the link's taps
+            const int64_t seg = ss->plan->d.aeq_segment;
+            for (int64_t k = 0; k < r.n_sym; k += seg) {
+                AeqChain c{};
+                c.frame = i;
+                c.keep = k;
+                c.end = std::min(r.n_sym, k + seg);
+                c.begin = std::max<int64_t>(0, k - ss->plan->d.aeq_warmup);
+                c.write_state = c.end == r.n_sym;
+                c.init = (const int32_t *)(ss->arena_mem + r.off_init);
+                c.init_copy = -1;
+                w.chains.push_back(c);
+            }
         }
     }
     std::stable_sort(w.chains.begin(), w.chains.end(),
@@ -212,29 +243,29 @@ fnt_status launch_wave(fnt_session *ss, Slot &slot) {
     w.item_cut = {0, (int)w.items.size()};
     w.chain_cut = {0, (int)w.chains.size()};
     layout(w);
-    fnt_status st = grow(slot, w.total);
+    std::vector<StateCopy> copies;
+    for (const Request &r : slot.reqs)
+        if (segmented(ss->plan, r.n_sym))
+            copies.push_back({ss->d_state + (size_t)r.link * 16 * kAeqK, (int32_t *)(ss->arena_mem + r.off_init)});
+    const size_t off_copies = w.total;
+    const size_t bytes = off_copies + copies.size() * sizeof(StateCopy);
+    fnt_status st = grow(slot, bytes);
     if (st != FNT_OK) return st;
     memcpy(slot.h_tables + w.off_frames, w.frames.data(), w.frames.size() * sizeof(DevFrame));
     if (!w.items.empty()) memcpy(slot.h_tables + w.off_items, w.items.data(), w.items.size() * sizeof(int4));
     if (!w.chains.empty())
         memcpy(slot.h_tables + w.off_chains, w.chains.data(), w.chains.size() * sizeof(AeqChain));
-    cudaError_t e = cudaMemcpyAsync(slot.d_tables, slot.h_tables, w.off_scratch, cudaMemcpyHostToDevice, slot.stream);
+    if (!copies.empty()) memcpy(slot.h_tables + off_copies, copies.data(), copies.size() * sizeof(StateCopy));
+    cudaError_t e = cudaMemcpyAsync(slot.d_tables, slot.h_tables, bytes, cudaMemcpyHostToDevice, slot.stream);
     if (e != cudaSuccess) return cuda_fail(e, "session: table upload");
-    for (const Request &r : slot.reqs) {
-        if (r.host_io && r.n > 0) {
-            e = cudaMemcpyAsync(ss->arena_mem + r.off_in, r.in, (size_t)r.n * 4, cudaMemcpyHostToDevice, slot.stream);
-            if (e != cudaSuccess) return cuda_fail(e, "session: input copy");
-        }
+    if (!copies.empty()) {
+        copy_states<<<std::min<int>((int)copies.size(), 1024), 256, 0, slot.stream>>>(
+            (const StateCopy *)(slot.d_tables + off_copies), (int)copies.size());
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "session: state copy launch");
     }
     st = launch_work(ss->plan, w, slot.d_tables, slot.stream);
     if (st != FNT_OK) return st;
-    for (const Request &r : slot.reqs) {
-        if (r.host_io && r.n_sym > 0) {
-            e = cudaMemcpyAsync(r.out, ss->arena_mem + r.off_out, (size_t)r.n_sym * 8, cudaMemcpyDeviceToHost,
-                                slot.stream);
-            if (e != cudaSuccess) return cuda_fail(e, "session: output copy");
-        }
-    }
     e = cudaEventRecord(slot.done, slot.stream);
     if (e != cudaSuccess) return cuda_fail(e, "session: event record");
     return FNT_OK;
@@ -298,16 +329,19 @@ void reap(fnt_session *ss) {
     }
 }
 
-bool is_device_ptr(const void *p, bool &pinned_host) {
+// Device-accessible address of a buffer: device (or managed) memory as it is,
+// page-locked host memory through its device mapping (on GB300 the GPU reads
+// and writes Grace memory coherently over NVLink-C2C); nullptr for pageable
+// host memory.
+void *device_view(const void *p) {
     cudaPointerAttributes a;
-    pinned_host = false;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return nullptr;
     }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return true;
-    pinned_host = a.type == cudaMemoryTypeHost;
-    return false;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return const_cast<void *>(p);
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
 }
 
 }  // namespace
@@ -386,19 +420,18 @@ extern "C" fnt_status fnt_session_submit(fnt_session *ss, int32_t link, const vo
     r.n = n;
     r.n_sym = chain_nsym(n, lk.phase);
     if (n > 0) {
-        bool pin_in = false, pin_out = false;
-        const bool dev_in = is_device_ptr(in, pin_in), dev_out = is_device_ptr(out, pin_out);
-        if (dev_in != dev_out || (!dev_in && !(pin_in && pin_out)))
-            return fail(FNT_ERR_INVALID, "submit: in/out must both be device or both page-locked host memory");
-        r.host_io = !dev_in;
-        if (((uintptr_t)in % 4) || ((uintptr_t)out % 4)) return fail(FNT_ERR_INVALID, "submit: 4-byte alignment");
+        void *din = device_view(in), *dout = device_view(out);
+        if (!din || !dout)
+            return fail(FNT_ERR_INVALID, "submit: in/out must be device memory or page-locked host memory");
+        if (((uintptr_t)din % 4) || ((uintptr_t)dout % 4)) return fail(FNT_ERR_INVALID, "submit: 4-byte alignment");
+        r.in = (const int8_t *)din;
+        r.out = dout;
     }
-    r.bytes = std::max<size_t>(256, request_bytes(r));
+    r.bytes = std::max<size_t>(256, request_bytes(ss->plan, r));
     if (r.bytes > ss->cap) return fail(FNT_ERR_BOUND, "submit: frame needs %zu bytes > cap %zu", r.bytes, ss->cap);
     if (!ss->arena.alloc(r.bytes, r.off)) return fail(FNT_ERR_BUSY, "submit: memory cap reached");
     r.off_scratch = r.off;
-    r.off_in = r.off + up256((size_t)r.n_sym * 4);
-    r.off_out = r.off_in + up256((size_t)r.n * 4);
+    r.off_init = r.off + up256((size_t)r.n_sym * 4);
     r.ticket = ss->next_ticket++;
     r.submit_us = now_us();
     lk.fifo.push_back(r);

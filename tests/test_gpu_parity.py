@@ -46,11 +46,15 @@ def test_cdc_random_matches_oracle(orc, n, n_pol, L):
     assert np.array_equal(got, orc.cdc(x, taps) if n else np.zeros((0, n_pol, 2), np.int32))
 
 
-@pytest.mark.parametrize("step", [32, 40, 48])
-def test_cdc_custom_step(orc, step):
-    rng = np.random.default_rng(step)
+@pytest.mark.parametrize("step,L", [(32, 17), (40, 17), (48, 17), (32, 31), (34, 31)])
+def test_cdc_custom_step(orc, step, L):
+    """Includes the Tab. 1 operating point: 50 % overlap (S = 32) with up to
+    31 taps, worst-case magnitudes included."""
+    rng = np.random.default_rng(step + L)
     x = rng.integers(-16, 16, (4000, 2, 2)).astype(np.int8)
-    taps = rng.integers(-32, 32, (17, 2)).astype(np.int8)
+    x[:700] = -16
+    taps = rng.integers(-32, 32, (L, 2)).astype(np.int8)
+    taps[: L // 2] = -32
     got = run_cdc(F.Plan(cdc_step=step), x, taps)
     assert np.array_equal(got, orc.cdc(x, taps, 64, 4080, step))
 

@@ -132,3 +132,24 @@ def test_single_rank_reduce_is_identity():
     import bench
     assert bench.reduce_max(1.25) == 1.25
     assert bench.aggregate(2 ** 21, 1, 1e-3) == pytest.approx(2 ** 21 / 1e-3 / 1e9)
+
+
+def test_tab1_multiplication_counts():
+    """Tab. 1: FNT-CDC 8 and FNT-AEQ 64 real multiplications per symbol at the
+    paper's operating point (64-point CDC with 50 % overlap, 32-point AEQ),
+    from the kernels' own per-block counts.  The FD / TD rows and the
+    complexity reductions of the text are context (evaluated here from the
+    table's formulas)."""
+    import math
+    import paper_2405_04253_gb300 as fnt
+    oc = fnt.op_counts(17, cdc_step=32, n_aeq=32, alpha_aeq=2)
+    assert oc["cdc_mults_per_symbol"] == 8
+    assert oc["aeq_mults_per_symbol"] == 64
+    fd_cdc = lambda n: 12 * math.log2(n) + 12
+    fd_aeq = lambda n: 24 * math.log2(n) + 32
+    assert round(1 - 64 / fd_aeq(32), 2) == 0.58                    # AEQ: -58 %
+    assert round(1 - 8 / fd_cdc(32), 2) == 0.89                     # CDC: -89 % (at log2 N = 5)
+    assert round(1 - (8 + 64) / (fd_cdc(32) + fd_aeq(32)), 2) == 0.68
+    # the default step N - L + 1 spends fewer products per symbol
+    assert fnt.op_counts(17)["cdc_mults_per_symbol"] == 128 / 24
+    assert fnt.op_counts(17, n_aeq=64, alpha_aeq=4080)["aeq_mults_per_symbol"] == 32 * 64 / 48
