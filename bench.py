@@ -220,7 +220,7 @@ class OraclePool:
 
 def _prm_kw(wl):
     return dict(n_aeq=wl["n_aeq"], alpha_aeq=wl["alpha_aeq"], mu_shift=MU_SHIFT, seg_len=wl["segment"],
-                warmup=wl["warmup"])
+                warmup=wl["warmup"], period=wl.get("period", 1))
 
 
 def _segments(x_np, taps, wl, n_seg):
@@ -246,7 +246,7 @@ def run_fnt(args, rank, world, local_rank):
     L = taps.shape[0]
     S = 64 - L + 1
     plan = fnt.Plan(n_aeq=wl["n_aeq"], alpha_aeq=wl["alpha_aeq"], mu_shift=MU_SHIFT,
-                    aeq_segment=wl["segment"], aeq_warmup=wl["warmup"])
+                    aeq_segment=wl["segment"], aeq_warmup=wl["warmup"], aeq_update_period=wl.get("period", 1))
     nsym = fnt.chain_nsym(n, L)
     x = torch.from_numpy(x_np).to(dev)
     out = torch.zeros((nsym, 4), dtype=torch.int16, device=dev)
@@ -367,7 +367,8 @@ def run_fnt(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload + ": " + wl["desc"], "samples_per_step": n, "symbols_per_step": nsym,
+        "config": {"workload": args.workload + ": " + wl["desc"], "aeq_update_period": wl.get("period", 1),
+                   "samples_per_step": n, "symbols_per_step": nsym,
                    "l2": "flushed between timed steps (256 MiB write outside the events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "aeq_mu_shift": MU_SHIFT, "rde_a": 64},
@@ -642,7 +643,11 @@ def main(argv=None):
     ap.add_argument("--cpu-segments", type=int, default=128)
     ap.add_argument("--ref-segments", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--aeq-period", type=int, default=1,
+                    help="cfg2 / cfg5: AEQ blocks per tap update (1 = every block, as in eq. (6))")
     args = ap.parse_args(argv)
+    for wl in WORKLOADS.values():
+        wl["period"] = args.aeq_period
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -88,6 +88,12 @@ FNT_API const char *fnt_version(void);
  *                    slice were a frame of its own; only the segment's own
  *                    outputs are kept.  Segments run in parallel.
  * aeq_warmup         warm-up symbols of each segment (ignored without segments).
+ * aeq_update_period  P, AEQ blocks per tap update, 0..64 (0 and 1: every block,
+ *                    the paper's eq. (6) schedule).  For P > 1 the gradient G of
+ *                    eq. (6) is summed over P blocks of a run (a frame, or a
+ *                    segment counted from its warm-up start) and applied as
+ *                    floor(sum / 2^m) after every P-th block and after the
+ *                    run's last block; the taps are fixed in between.
  */
 typedef struct fnt_plan_desc {
     int32_t n_cdc;
@@ -99,13 +105,13 @@ typedef struct fnt_plan_desc {
     int32_t mu_shift;
     int32_t rde_a;
     int32_t tap_init;
-    int32_t reserved;
+    int32_t aeq_update_period;
     int64_t aeq_segment;
     int64_t aeq_warmup;
 } fnt_plan_desc;
 
 /* Fills *desc with the defaults: N=64/4080, S = N-L+1, AEQ N=32/2, K=16, m=10,
- * A=64, w0=2048, no segments. */
+ * A=64, w0=2048, no segments, an update every block. */
 FNT_API void fnt_plan_desc_default(fnt_plan_desc *desc);
 
 typedef struct fnt_plan fnt_plan;

@@ -327,13 +327,16 @@ void orc_aeq_init_taps(int K, int w0, int32_t *T) {
  * r^2 < 14A^2, else 18A^2 (the 16QAM rings); e_p = R - r^2.  After the block,
  *   G[S2][S1][k] = sum_t e_p(S2)[t] z_S2[t] x_S1[t - k]   (valid t of the block)
  *   T <- clamp(T + floor(G / 2^m), -2^29, 2^29 - 1).
- * m >= 63 stands for mu = 0 (taps held fixed).  Returns 0 on success.
+ * m >= 63 stands for mu = 0 (taps held fixed).  With an update period P > 1
+ * (the paper updates every step, P = 1) G is summed over P blocks and the
+ * update is applied after every P-th block and after the last block; the taps
+ * stay fixed in between.  Returns 0 on success.
  */
 int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, int rde_a,
-            int32_t *T, int16_t *out, int use_fnt) {
+            int32_t *T, int16_t *out, int use_fnt, int period) {
     const i64 F = 65537;
     const int S = N - K;
-    if (n_sym < 0 || K < 1 || S < 1 || N > 256 || mu_shift < 0 || rde_a < 1) return 1;
+    if (n_sym < 0 || K < 1 || S < 1 || N > 256 || mu_shift < 0 || rde_a < 1 || period < 1) return 1;
     xform t;
     if (use_fnt && xform_init(&t, N, alpha, F) != 0) return 2;
     const i64 A2 = (i64)rde_a * rde_a;
@@ -348,6 +351,7 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
     i64 *z = malloc(sizeof(i64) * S * 4);
     i64 *e = malloc(sizeof(i64) * S * 2);
     int *W = malloc(sizeof(int) * 16 * K);
+    i64 *Gacc = calloc(16 * K, sizeof(i64));     /* gradient summed over the update period */
 
     const i64 nblk = (n_sym + S - 1) / S;
     for (i64 blk = 0; blk < nblk; ++blk) {
@@ -411,6 +415,8 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
             }
         }
 
+        /* the update is applied after every period-th block and after the last one */
+        const int apply = ((blk + 1) % period == 0) || (blk == nblk - 1);
         for (int s2 = 0; s2 < 4; ++s2)
             for (int s1 = 0; s1 < 4; ++s1)
                 for (int k = 0; k < K; ++k) {
@@ -420,12 +426,17 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
                         const i64 xv = tt >= 0 ? x[tt * 4 + s1] : 0;
                         G += e[(s2 / 2) * S + i] * z[s2 * S + i] * xv;
                     }
+                    const int f = (s2 * 4 + s1) * K + k;
+                    Gacc[f] += G;
+                    if (!apply) continue;
+                    const i64 Gp = Gacc[f];
+                    Gacc[f] = 0;
                     if (mu_shift >= 63) continue;               /* mu = 0: fixed taps */
-                    int32_t *Tp = T + (s2 * 4 + s1) * K + k;
-                    *Tp = (int32_t)clampll((i64)*Tp + floor_shift(G, mu_shift),
-                                           -((i64)1 << 29), ((i64)1 << 29) - 1);
+                    T[f] = (int32_t)clampll((i64)T[f] + floor_shift(Gp, mu_shift), -((i64)1 << 29),
+                                            ((i64)1 << 29) - 1);
                 }
     }
+    free(Gacc);
     free(win); free(Xf); free(wv); free(Wf); free(P); free(c); free(y); free(z); free(e); free(W);
     if (use_fnt) xform_free(&t);
     return 0;
@@ -441,7 +452,7 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
  */
 int orc_aeq_segmented(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift,
                       int rde_a, const int32_t *T0, i64 seg_len, i64 warmup, int32_t *T_out,
-                      int16_t *out, int use_fnt) {
+                      int16_t *out, int use_fnt, int period) {
     int32_t *T = malloc(sizeof(int32_t) * 16 * K);
     int rc = 0;
     if (seg_len <= 0) seg_len = n_sym > 0 ? n_sym : 1;
@@ -452,7 +463,7 @@ int orc_aeq_segmented(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int m
         const i64 begin = keep - warmup > 0 ? keep - warmup : 0;
         int16_t *tmp = malloc(sizeof(int16_t) * 4 * (end - begin));
         memcpy(T, T0, sizeof(int32_t) * 16 * K);
-        rc = orc_aeq(x + begin * 4, end - begin, N, alpha, K, mu_shift, rde_a, T, tmp, use_fnt);
+        rc = orc_aeq(x + begin * 4, end - begin, N, alpha, K, mu_shift, rde_a, T, tmp, use_fnt, period);
         memcpy(out + keep * 4, tmp + (keep - begin) * 4, sizeof(int16_t) * 4 * (end - keep));
         free(tmp);
     }

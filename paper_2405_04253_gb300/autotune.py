@@ -21,7 +21,7 @@ def _key(plan: Plan, frames, op: int) -> str:
     lens = sorted(int(f.n) for f in frames)
     total = sum(lens)
     return (f"op{op}_n{len(frames)}_tot{total}_max{lens[-1] if lens else 0}_aeq{d.n_aeq}"
-            f"_seg{d.aeq_segment}_{d.aeq_warmup}")
+            f"_seg{d.aeq_segment}_{d.aeq_warmup}_p{d.aeq_update_period}")
 
 
 def _time_stage(batch: Batch, stage: int, reps: int, stream) -> float:

@@ -21,7 +21,10 @@
 // a filter hold them), accumulates the gradient of 4 of them, and the four
 // lanes swap their updated quarters.  The input spectra (taps-independent) are
 // computed 8 blocks ahead, one full N-point transform per lane, with N^-1
-// folded in.
+// folded in.  With an update period P > 1 the gradient is summed over P blocks
+// and applied after every P-th block and the last one; in between the taps do
+// not change, so each lane keeps its tap half-spectrum in shared memory and
+// transforms the taps once per period.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -46,6 +49,7 @@ struct AeqCfg {
     static constexpr int ZS = 2 * SA;
     static constexpr int ES = SA;
     static constexpr int WORDS = 2 * XS + XF + RED + ZS + ES;  // xs double-buffered
+    static constexpr int WCACHE = 32 * M;                    // tap half-spectra [M][lane], P > 1 only
     static constexpr int32_t NINV = zcent(zinv(NA));
     static constexpr int64_t ALPHA2 = ALPHA * ALPHA % kF;    // radix of the half transforms
     static constexpr int64_t AINV = zinv(ALPHA);
@@ -116,7 +120,9 @@ struct JoinHalves {
     }
 };
 
-template <int NA, int64_t ALPHA>
+// PER: update period P > 1 (gradient summed over P blocks, tap spectra cached);
+// the P = 1 instance is the per-block update with no period bookkeeping.
+template <int NA, int64_t ALPHA, bool PER>
 __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ frames,
                                                   const AeqChain *__restrict__ chains, int n_items,
                                                   AeqParams prm) {
@@ -128,11 +134,14 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    uint32_t *xs2 = smem + warp * C::WORDS;       // two staging buffers of C::XS words
+    const int period = PER ? prm.period : 1;
+    const int words = C::WORDS + (PER ? C::WCACHE : 0);
+    uint32_t *xs2 = smem + warp * words;          // two staging buffers of C::XS words
     int32_t *xf = (int32_t *)(xs2 + 2 * C::XS);
     int32_t *red = xf + C::XF;
     int32_t *zs = red + C::RED;
     int32_t *es = zs + C::ZS;
+    int32_t *wcache = es + C::ES + lane;          // stride 32: conflict-free
 
     const int h = lane & 1;                   // frequency parity held by this lane
     const int task = lane >> 1;
@@ -157,6 +166,8 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
         for (int k = 0; k < K; ++k) T[k] = ch.init[(s2 * 4 + s1) * K + k];
 
         const int64_t nblk = (ch.end - ch.begin + SA - 1) / SA;
+        int64_t acc[4] = {0, 0, 0, 0};            // gradient of taps k0 .. k0 + 3 over the period
+        int in_period = 0;                        // blocks of the current period done
         // input symbols of batch 0 (PRE blocks + K history); later batches are
         // prefetched one batch ahead into the other buffer
         __syncwarp();
@@ -193,21 +204,30 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                 __syncwarp();
             }
 
-            // tap group -> even / odd half spectrum in this lane
-            int32_t wv[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const int32_t W = T[k] >> 16;
-                wv[k] = g ? (W & 127) : (W >> 7);
-            }
+            // tap group -> even / odd half spectrum in this lane (once per period)
             int32_t y[M];
-            SplitTaps<NA, ALPHA, 0>::run(y, wv, odd);
+            if (!PER || in_period == 0) {
+                int32_t wv[K];
 #pragma unroll
-            for (int j = K; j < M; ++j) y[j] = 0;
-            if constexpr (M >= 2 * K)
-                fnt_fwd_halfzero<M, C::ALPHA2, 17>(y);
-            else
-                fnt_fwd<M, C::ALPHA2, 17>(y);
+                for (int k = 0; k < K; ++k) {
+                    const int32_t W = T[k] >> 16;
+                    wv[k] = g ? (W & 127) : (W >> 7);
+                }
+                SplitTaps<NA, ALPHA, 0>::run(y, wv, odd);
+#pragma unroll
+                for (int j = K; j < M; ++j) y[j] = 0;
+                if constexpr (M >= 2 * K)
+                    fnt_fwd_halfzero<M, C::ALPHA2, 17>(y);
+                else
+                    fnt_fwd<M, C::ALPHA2, 17>(y);
+                if constexpr (PER) {
+#pragma unroll
+                    for (int j = 0; j < M; ++j) wcache[32 * j] = y[j];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < M; ++j) y[j] = wcache[32 * j];
+            }
             const int32_t *xrow = xf + (bb * 4 + s1) * C::XF_ROW + h * C::HALF;
 #pragma unroll
             for (int j = 0; j < M; ++j) y[j] = rho(rhoc(y[j]) * xrow[j]);
@@ -248,13 +268,15 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
             }
             __syncwarp();
 
-            // eq. (6): G[k] = sum_i e[i] z_S2[i] x_S1[t0 + i - k] for k = k0 .. k0 + 3
+            // eq. (6): G[k] = sum_i e[i] z_S2[i] x_S1[t0 + i - k] for k = k0 .. k0 + 3,
+            // summed over the blocks of the update period
+            const bool apply = !PER || ++in_period == period || blk + 1 == nblk;
+            if (PER && apply) in_period = 0;
             if (mu < 63) {
                 // rolling window: w0..w3 = x_S1[t0 + i - k0 - kk], kk = 0..3, read
                 // as sign-extending byte loads of stream s1 from the staged words
                 const int8_t *xb = (const int8_t *)(xs + bb * SA + K - k0) + s1;
                 int32_t w1 = xb[-4], w2 = xb[-8], w3 = xb[-12];
-                int64_t acc[4] = {0, 0, 0, 0};
                 const int32_t *zrow = zs + o * SA;
 #pragma unroll 4
                 for (int i = 0; i < SA; ++i) {
@@ -270,29 +292,32 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                     w2 = w1;
                     w1 = w0;
                 }
-                int32_t nv[4];
+                if (apply) {
+                    int32_t nv[4];
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const int32_t cur = h ? (g ? T[12 + kk] : T[4 + kk]) : (g ? T[8 + kk] : T[kk]);
-                    int64_t v = (int64_t)cur + (acc[kk] >> mu);
-                    v = v < -(1ll << 29) ? -(1ll << 29) : (v > (1ll << 29) - 1 ? (1ll << 29) - 1 : v);
-                    nv[kk] = (int32_t)v;
-                }
-                // gather the filter's 16 taps from its four lanes (lane bit 0 = h, bit 1 = g)
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int32_t cur = h ? (g ? T[12 + kk] : T[4 + kk]) : (g ? T[8 + kk] : T[kk]);
+                        int64_t v = (int64_t)cur + (acc[kk] >> mu);
+                        v = v < -(1ll << 29) ? -(1ll << 29) : (v > (1ll << 29) - 1 ? (1ll << 29) - 1 : v);
+                        nv[kk] = (int32_t)v;
+                        acc[kk] = 0;
+                    }
+                    // gather the filter's 16 taps from its four lanes (lane bit 0 = h, bit 1 = g)
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const int32_t a = nv[kk];                                 // (g, h)
-                    const int32_t b = __shfl_xor_sync(0xffffffffu, a, 1);     // (g, 1-h)
-                    const int32_t c2 = __shfl_xor_sync(0xffffffffu, a, 2);    // (1-g, h)
-                    const int32_t d = __shfl_xor_sync(0xffffffffu, b, 2);     // (1-g, 1-h)
-                    const int32_t q00 = g ? (h ? d : c2) : (h ? b : a);       // g=0, h=0
-                    const int32_t q01 = g ? (h ? c2 : d) : (h ? a : b);       // g=0, h=1
-                    const int32_t q10 = g ? (h ? b : a) : (h ? d : c2);       // g=1, h=0
-                    const int32_t q11 = g ? (h ? a : b) : (h ? c2 : d);       // g=1, h=1
-                    T[kk] = q00;
-                    T[4 + kk] = q01;
-                    T[8 + kk] = q10;
-                    T[12 + kk] = q11;
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int32_t a = nv[kk];                                 // (g, h)
+                        const int32_t b = __shfl_xor_sync(0xffffffffu, a, 1);     // (g, 1-h)
+                        const int32_t c2 = __shfl_xor_sync(0xffffffffu, a, 2);    // (1-g, h)
+                        const int32_t d = __shfl_xor_sync(0xffffffffu, b, 2);     // (1-g, 1-h)
+                        const int32_t q00 = g ? (h ? d : c2) : (h ? b : a);       // g=0, h=0
+                        const int32_t q01 = g ? (h ? c2 : d) : (h ? a : b);       // g=0, h=1
+                        const int32_t q10 = g ? (h ? b : a) : (h ? d : c2);       // g=1, h=0
+                        const int32_t q11 = g ? (h ? a : b) : (h ? c2 : d);       // g=1, h=1
+                        T[kk] = q00;
+                        T[4 + kk] = q01;
+                        T[8 + kk] = q10;
+                        T[12 + kk] = q11;
+                    }
                 }
             }
         }
@@ -310,16 +335,24 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
 // tap groups x N (each split over two lanes as two N/2 halves).
 int aeq_mults_per_block(int na) { return 32 * na; }
 
-size_t aeq_smem_bytes(int na, int warps) {
-    return (size_t)warps * (na == 64 ? AeqCfg<64, 4080>::WORDS : AeqCfg<32, 2>::WORDS) * sizeof(uint32_t);
+size_t aeq_smem_bytes(int na, int warps, int period) {
+    const int words = na == 64 ? AeqCfg<64, 4080>::WORDS + (period > 1 ? AeqCfg<64, 4080>::WCACHE : 0)
+                               : AeqCfg<32, 2>::WORDS + (period > 1 ? AeqCfg<32, 2>::WCACHE : 0);
+    return (size_t)warps * words * sizeof(uint32_t);
+}
+
+template <int NA, int64_t ALPHA, bool PER>
+static cudaError_t aeq_configure_one() {
+    return cudaFuncSetAttribute(aeq_kernel<NA, ALPHA, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)aeq_smem_bytes(NA, 4, PER ? 2 : 1));
 }
 
 cudaError_t aeq_configure() {
-    cudaError_t e = cudaFuncSetAttribute(aeq_kernel<64, 4080>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)aeq_smem_bytes(64, 4));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(aeq_kernel<32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)aeq_smem_bytes(32, 4));
+    cudaError_t e = aeq_configure_one<64, 4080, false>();
+    if (e == cudaSuccess) e = aeq_configure_one<64, 4080, true>();
+    if (e == cudaSuccess) e = aeq_configure_one<32, 2, false>();
+    if (e == cudaSuccess) e = aeq_configure_one<32, 2, true>();
+    return e;
 }
 
 // Work items are (chain, polarisation) pairs: 2 per chain.
@@ -327,13 +360,18 @@ cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, i
                        int warps, int grid, cudaStream_t stream) {
     if (n_chains <= 0) return cudaSuccess;
     const dim3 block(32 * warps);
-    const size_t smem = aeq_smem_bytes(na, warps);
+    const size_t smem = aeq_smem_bytes(na, warps, prm.period);
     const int n_items = 2 * n_chains;
     if (grid <= 0) grid = (n_items + warps - 1) / warps;
-    if (na == 64)
-        aeq_kernel<64, 4080><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+    const bool per = prm.period > 1;
+    if (na == 64 && per)
+        aeq_kernel<64, 4080, true><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+    else if (na == 64)
+        aeq_kernel<64, 4080, false><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+    else if (per)
+        aeq_kernel<32, 2, true><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
     else
-        aeq_kernel<32, 2><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+        aeq_kernel<32, 2, false><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
     return cudaGetLastError();
 }
 

@@ -104,6 +104,7 @@ extern "C" void fnt_plan_desc_default(fnt_plan_desc *d) {
     d->tap_init = 2048;
     d->aeq_segment = 0;
     d->aeq_warmup = 0;
+    d->aeq_update_period = 0;
 }
 
 static bool g_configured = false;
@@ -136,6 +137,8 @@ extern "C" fnt_status fnt_plan_create(const fnt_plan_desc *d, fnt_plan **out) {
     if (d->rde_a < 1 || d->rde_a > 4096) return fail(FNT_ERR_INVALID, "rde_a must be in [1, 4096]");
     if (d->tap_init < -8192 || d->tap_init > 8191) return fail(FNT_ERR_INVALID, "tap_init must be a 14-bit tap");
     if (d->aeq_segment < 0 || d->aeq_warmup < 0) return fail(FNT_ERR_INVALID, "negative AEQ segment/warmup");
+    if (d->aeq_update_period < 0 || d->aeq_update_period > kMaxUpdatePeriod)
+        return fail(FNT_ERR_INVALID, "aeq_update_period must be in [0, %d]", kMaxUpdatePeriod);
     fnt_status st = configure_kernels();
     if (st != FNT_OK) return st;
 
@@ -437,7 +440,7 @@ static fnt_status launch_aeq_range(const fnt_plan *p, const Work &w, const char 
                                    cudaStream_t stream) {
     if (c1 <= c0) return FNT_OK;
     const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
-    AeqParams prm{p->d.mu_shift, p->d.rde_a};
+    AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d)};
     cudaError_t e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(dev + w.off_chains) + c0, c1 - c0, prm,
                                p->aeq_warps, 0, stream);
     return e == cudaSuccess ? FNT_OK : cuda_fail(e, "aeq kernel launch");

@@ -45,6 +45,9 @@ struct Work {
 
 constexpr size_t kStateBytes = 16 * kAeqK * sizeof(int32_t);
 
+// Blocks per AEQ tap update: 0 in the descriptor means every block.
+inline int update_period(const fnt_plan_desc &d) { return d.aeq_update_period > 1 ? d.aeq_update_period : 1; }
+
 fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work &w);
 void layout(Work &w);
 fnt_status upload_work(Work &w, char *dev, cudaStream_t stream);
@@ -63,7 +66,7 @@ int aeq_mults_per_block(int na);
 cudaError_t cdc_configure();
 cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, int warps, int grid,
                        cudaStream_t stream);
-size_t aeq_smem_bytes(int na, int warps);
+size_t aeq_smem_bytes(int na, int warps, int period);
 cudaError_t aeq_configure();
 cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,
                        int warps, int grid, cudaStream_t stream);

@@ -47,6 +47,9 @@ static_assert(sizeof(AeqChain) == 48, "AeqChain layout");
 struct AeqParams {
     int32_t mu_shift;
     int32_t rde_a;
+    int32_t period;       // blocks per tap update, >= 1
 };
+
+constexpr int kMaxUpdatePeriod = 64;   // keeps the summed int64 gradient exact
 
 }  // namespace fnt

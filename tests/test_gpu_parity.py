@@ -173,6 +173,43 @@ def test_aeq_segmented_matches_oracle(orc, na, alpha):
     assert np.array_equal(got2, ref2)
 
 
+@pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
+@pytest.mark.parametrize("period,n", [(2, 1000), (3, 333), (5, 4099), (64, 5000), (64, 700), (4, 16)])
+def test_aeq_update_period_matches_oracle(orc, na, alpha, period, n):
+    """Update period P: the summed gradient of P blocks is applied after every
+    P-th block and the last; the taps (and their cached spectra) are fixed in
+    between."""
+    rng = np.random.default_rng(na + 7 * period + n)
+    x = rng.integers(-16, 16, (n, 4)).astype(np.int8)
+    T0 = orc.aeq_init_taps(16, 2048) + rng.integers(-(1 << 20), 1 << 20, (4, 4, 16)).astype(np.int32)
+    plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=12, aeq_update_period=period)
+    got, Tg = run_aeq(plan, x, T0)
+    ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=12, rde_a=64, period=period)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(Tg, Tr)
+    if n > 2 * (na - 16) and period < 64:
+        every, _ = orc.aeq(x, T0, na, alpha, mu_shift=12, rde_a=64)
+        assert not np.array_equal(ref, every)           # the case exercises the period
+
+
+@pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
+def test_chain_segmented_update_period_matches_oracle(orc, na, alpha):
+    """Periods count from each segment's warm-up start."""
+    f = synth.config2(1 << 13)
+    kw = dict(n_aeq=na, alpha_aeq=alpha, mu_shift=9)
+    plan = F.Plan(aeq_segment=1000, aeq_warmup=120, aeq_update_period=4, **kw)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    out = i16((nsym, 4))
+    T0 = orc.aeq_init_taps(16, 2048)
+    st = dev(T0)
+    F.cdc_aeq_run(plan, [F.Frame(dev(f.x), out, f.taps, st)])
+    torch.cuda.synchronize()
+    prm = orc.ChainParams(seg_len=1000, warmup=120, period=4, **kw)
+    ref, Tr = orc.chain(f.x, f.taps, prm, T0=T0)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    assert np.array_equal(st.cpu().numpy(), Tr)
+
+
 def test_chain_segmented_state_carried_over_calls(orc):
     """A long stream processed call after call: each call's segments start from
     the taps the previous call ended with."""

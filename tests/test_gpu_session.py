@@ -201,16 +201,17 @@ def test_session_rejects_pageable_host_buffers():
     s.close()
 
 
-def test_session_segmented_plan_matches_sequential_oracle(orc):
+@pytest.mark.parametrize("period", [1, 2])
+def test_session_segmented_plan_matches_sequential_oracle(orc, period):
     """With AEQ segments in the plan, each served frame's segments start from
     the link's taps as the frame began; per link this equals sequential oracle
-    processing with the same segment rule."""
+    processing with the same segment rule (and update period)."""
     rng = np.random.default_rng(26)
     links = make_links(rng, 4)
     frames = make_frames(rng, 4, 3, lo=4000, hi=12000)
-    plan = F.Plan(mu_shift=MU, aeq_segment=512, aeq_warmup=16)
+    plan = F.Plan(mu_shift=MU, aeq_segment=512, aeq_warmup=16, aeq_update_period=period)
     got, Tgot = run_session(plan, links, frames)
-    prm = orc.ChainParams(mu_shift=MU, seg_len=512, warmup=16)
+    prm = orc.ChainParams(mu_shift=MU, seg_len=512, warmup=16, period=period)
     T = {l: orc.aeq_init_taps(16, prm.w0) for l in range(len(links))}
     for i, (link, x) in enumerate(frames):
         ref, T[link] = orc.chain(x, links[link], prm, T0=T[link])

@@ -69,6 +69,11 @@ def test_plan_rejects_invalid_radix_without_gpu():
     with pytest.raises(fnt.FntError) as e:
         fnt.Plan(n_aeq=32, alpha_aeq=4)            # order 16: alpha^32 = 1 but order != 32
     assert e.value.status == fnt.FNT_ERR_BOUND
+    for bad in (-1, 65):                          # update period outside [0, 64]
+        with pytest.raises(fnt.FntError) as e:
+            fnt.Plan(aeq_update_period=bad)
+        assert e.value.status == fnt.FNT_ERR_INVALID
+    assert fnt.default_desc().aeq_update_period == 0
 
 
 def test_product_package_does_not_import_oracle():

@@ -328,3 +328,46 @@ def test_aeq_converges_on_synthetic_16qam(orc):
     e = np.mean(err, axis=0)
     q = len(e) // 4
     assert e[-q:].mean() < 0.85 * e[:q].mean()
+
+
+
+def test_aeq_update_period_rules(orc):
+    """Update period P: P = 1 is the per-block update.  For P > 1 the blocks of
+    one period see the same taps, and after every P-th block (and the last) the
+    taps move by floor(sum of the period's gradients / 2^m).  Rebuilt period by
+    period from fixed-tap runs: a run at m = 0 with one final update yields the
+    summed gradient of every block it covers under fixed taps, so the difference
+    of two such runs over nested prefixes is one period's gradient."""
+    rng = np.random.default_rng(13)
+    S, P, m = 16, 3, 8
+    x = rng.integers(-2, 3, (S * 7 + 5, 4)).astype(np.int8)     # 8 blocks, ragged tail
+    T0 = orc.aeq_init_taps(16, 2048)
+    a, Ta = orc.aeq(x, T0, 32, 2, mu_shift=m)
+    b, Tb = orc.aeq(x, T0, 32, 2, mu_shift=m, period=1)
+    assert np.array_equal(a, b) and np.array_equal(Ta, Tb)
+    got, Tg = orc.aeq(x, T0, 32, 2, mu_shift=m, period=P)
+    assert not np.array_equal(got, a)                            # the period changes the result
+    n = x.shape[0]
+    never = 1 << 30
+
+    def gsum(T, hi):
+        """Gradient summed over the blocks of x[:hi] under fixed taps T."""
+        if hi == 0:
+            return np.zeros(T.shape, np.int64)
+        _, Tn = orc.aeq(x[:hi], T, 32, 2, mu_shift=0, period=never)
+        assert np.abs(Tn).max() < (1 << 29) - 1                  # no clamp at m = 0
+        return Tn.astype(np.int64) - T.astype(np.int64)
+
+    T = T0.copy()
+    for lo in range(0, n, P * S):
+        hi = min(n, lo + P * S)
+        fixed, _ = orc.aeq(x[:hi], T, 32, 2, mu_shift=63)
+        assert np.array_equal(got[lo:hi], fixed[lo:hi]), lo
+        G = gsum(T, hi) - gsum(T, lo)
+        T = np.clip(T.astype(np.int64) + (G >> m), -(1 << 29), (1 << 29) - 1).astype(np.int32)
+    assert np.array_equal(Tg, T)
+    # P at least the block count: fixed taps throughout, one update at the end
+    out1, T1 = orc.aeq(x, T0, 32, 2, mu_shift=m, period=8)
+    fixed, _ = orc.aeq(x, T0, 32, 2, mu_shift=63)
+    assert np.array_equal(out1, fixed)
+    assert np.array_equal(T1, (T0.astype(np.int64) + (gsum(T0, n) >> m)).astype(np.int32))

@@ -47,9 +47,10 @@ def test_noalloc_equals_allocating_entry_point_twice_segmented():
         assert torch.equal(st_new, st_ref), call
 
 
-def test_noalloc_equals_allocating_entry_point_twice_with_state():
+@pytest.mark.parametrize("period", [1, 3])
+def test_noalloc_equals_allocating_entry_point_twice_with_state(period):
     rng = np.random.default_rng(31)
-    plan = F.Plan(mu_shift=9)
+    plan = F.Plan(mu_shift=9, aeq_update_period=period)
     init = torch.zeros((4, 4, 16), dtype=torch.int32, device="cuda")
     init[[0, 1, 2, 3], [0, 1, 2, 3], 8] = 2048 << 16
     st_ref, st_new = init.clone(), init.clone()
