@@ -19,12 +19,15 @@
 // the first half, so the forward split needs no shuffle at all.
 // Each lane holds the 16 master taps of its filter S1 -> S2 (all four lanes of
 // a filter hold them), accumulates the gradient of 4 of them, and the four
-// lanes swap their updated quarters.  The input spectra (taps-independent) are
+// lanes swap their updated quarters.  The gradient itself, a (4 inputs x 16
+// taps) x symbols x (2 outputs) contraction, runs exactly on the tensor cores
+// (gradient_mma below).  The input spectra (taps-independent) are
 // computed 8 blocks ahead, one full N-point transform per lane, with N^-1
 // folded in.  With an update period P > 1 the gradient is summed over P blocks
 // and applied after every P-th block and the last one; in between the taps do
 // not change, so each lane keeps its tap half-spectrum in shared memory and
 // transforms the taps once per period.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -45,11 +48,15 @@ struct AeqCfg {
     static constexpr int XF_ROW = 2 * HALF + 1;              // conflict-free: rows 3 banks apart
     static constexpr int XF = PRE * 4 * XF_ROW;              // input spectra [PRE][4][2][M]
     static constexpr int RED_ROW = SA + 1;
-    static constexpr int RED = 16 * RED_ROW;                 // per-task weighted outputs
-    static constexpr int ZS = 2 * SA;
-    static constexpr int ES = SA;
-    static constexpr int WORDS = 2 * XS + XF + RED + ZS + ES;  // xs double-buffered
+    static constexpr int GS = 4 * K * 8;                     // gradient limb sums [S1][k][o, limb]
+    static constexpr int RED = 16 * RED_ROW > GS ? 16 * RED_ROW : GS;  // per-task outputs, then GS
+    static constexpr int KT = SA / 16;                       // k-steps of the gradient product
+    static constexpr int EZ_ROW = SA / 2 + 4;                // f16 pairs per limb row; conflict-free
+    static constexpr int EZ = 8 * EZ_ROW;                    // e z limbs [o, limb][SA] as f16
+    static constexpr int WORDS = 2 * XS + XF + RED + EZ;     // xs double-buffered
     static constexpr int WCACHE = 32 * M;                    // tap half-spectra [M][lane], P > 1 only
+    static_assert(SA % 16 == 0 && (2 * XS + XF) % 4 == 0 && RED % 4 == 0 && WORDS % 4 == 0,
+                  "16-byte aligned regions");
     static constexpr int32_t NINV = zcent(zinv(NA));
     static constexpr int64_t ALPHA2 = ALPHA * ALPHA % kF;    // radix of the half transforms
     static constexpr int64_t AINV = zinv(ALPHA);
@@ -120,6 +127,98 @@ struct JoinHalves {
     }
 };
 
+// Gradient of eq. (6) on the tensor cores, exactly.  Per block and output o,
+//   G[S1][k][o] = sum_i A[S1][k][i] B[i][o],  A[S1][k][i] = x_S1[t0 + i - k],
+//   B[i][o] = e[i] z_o[i],
+// a (4 x 16) x SA x 2 product.  |e z| <= 2^31 * 2^15 = 2^46, so e z is split
+// into four balanced limbs c_l in [-2048, 2047] (e z = sum c_l 2^(12 l)); the
+// limbs and the 5-bit x are exact in f16, every product and every partial sum
+// of a block is an integer below 2^24 (2048 * 16 * 48 < 2^21), so the f32
+// accumulation is exact and the limb sums are recombined in int64.
+// Adding kLimbBias = 2048 (1 + 2^12 + 2^24 + 2^36) makes the limbs plain 12-bit
+// digits d_l = c_l + 2048 of a value in [0, 2^48).
+constexpr int64_t kLimbBias = 0x800800800800ll;
+
+__device__ __forceinline__ __half limb_half(uint32_t d) {
+    // d in [0, 4096): 2^23 + d exactly as f32, minus 2^23 + 2048, then to f16
+    return __float2half_rn(__int_as_float(0x4B000000u | d) - 8390656.0f);
+}
+
+// Limbs c_0 .. c_3 of u - kLimbBias (u = e z + kLimbBias) to col[l * RSH].
+template <int RSH>
+__device__ __forceinline__ void ez_limbs(int64_t u, __half *col) {
+    const uint32_t lo = (uint32_t)u, hi = (uint32_t)((uint64_t)u >> 32);
+    col[0] = limb_half(lo & 0xFFFu);
+    col[RSH] = limb_half((lo >> 12) & 0xFFFu);
+    col[2 * RSH] = limb_half(__funnelshift_r(lo, hi, 24) & 0xFFFu);
+    col[3 * RSH] = limb_half((hi >> 4) & 0xFFFu);
+}
+
+// f16 pair (x_S1[j], x_S1[j + 1]) from the staged words of symbols j, j + 1
+// (one byte per stream): 0x6400 + (x + 128) is 1152 + x in f16, exact for
+// any int8 x, and 1152 is subtracted exactly.
+template <int S1>
+__device__ __forceinline__ uint32_t x_pair(uint32_t wa, uint32_t wb) {
+    constexpr uint32_t sel = S1 | (S1 << 4) | ((4 + S1) << 8) | ((4 + S1) << 12);
+    uint32_t r = (__byte_perm(wa, wb, sel) & 0x00FF00FFu) ^ 0x64806480u;
+    __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&r), __halves2half2(__ushort_as_half(0x6480),
+                                                                                   __ushort_as_half(0x6480)));
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// One m-tile (input stream S1, taps 0..15) of the gradient product; the lane
+// holds rows k = gr, gr + 8 and limb columns 2 t, 2 t + 1 of the result.
+// A[k][i] = x[i - k] is Toeplitz: register pairs p[j] = x(2t - gr + 8 (j - 1) + {0, 1})
+// cover every fragment of the KT k-steps.
+template <class C, int S1>
+__device__ __forceinline__ void gradient_tile(const uint32_t (&wa)[2 * C::KT + 1], const uint32_t (&wb)[2 * C::KT + 1],
+                                              const uint32_t (&b0)[C::KT], const uint32_t (&b1)[C::KT],
+                                              int32_t *gs, int gr, int t) {
+    uint32_t pr[2 * C::KT + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * C::KT + 1; ++j) pr[j] = x_pair<S1>(wa[j], wb[j]);
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kt = 0; kt < C::KT; ++kt)
+        mma16816(d, pr[2 * kt + 1], pr[2 * kt], pr[2 * kt + 2], pr[2 * kt + 1], b0[kt], b1[kt]);
+    // every sum is an integer below 2^24: exact in f32 and in the conversion
+    *(int2 *)(gs + (S1 * C::K + gr) * 8 + 2 * t) = make_int2(__float2int_rn(d[0]), __float2int_rn(d[1]));
+    *(int2 *)(gs + (S1 * C::K + gr + 8) * 8 + 2 * t) = make_int2(__float2int_rn(d[2]), __float2int_rn(d[3]));
+}
+
+// gs[S1][k][4 o + l] = sum_i x_S1[t0 + i - k] c_l(e z_o)[i] for the block at xw
+// (xw[m] = staged word of symbol t0 + m, m >= -K).
+template <class C>
+__device__ __forceinline__ void gradient_mma(const uint32_t *xw, const uint32_t *ezh, int32_t *gs, int lane) {
+    const int gr = lane >> 2, t = lane & 3;
+    const uint32_t *xb = xw + 2 * t - gr - 8;
+    uint32_t wa[2 * C::KT + 1], wb[2 * C::KT + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * C::KT + 1; ++j) {
+        wa[j] = xb[8 * j];
+        wb[j] = xb[8 * j + 1];
+    }
+    uint32_t b0[C::KT], b1[C::KT];
+#pragma unroll
+    for (int kt = 0; kt < C::KT; ++kt) {
+        b0[kt] = ezh[gr * C::EZ_ROW + 8 * kt + t];
+        b1[kt] = ezh[gr * C::EZ_ROW + 8 * kt + 4 + t];
+    }
+    gradient_tile<C, 0>(wa, wb, b0, b1, gs, gr, t);
+    gradient_tile<C, 1>(wa, wb, b0, b1, gs, gr, t);
+    gradient_tile<C, 2>(wa, wb, b0, b1, gs, gr, t);
+    gradient_tile<C, 3>(wa, wb, b0, b1, gs, gr, t);
+}
+
 // PER: update period P > 1 (gradient summed over P blocks, tap spectra cached);
 // the P = 1 instance is the per-block update with no period bookkeeping.
 template <int NA, int64_t ALPHA, bool PER>
@@ -139,9 +238,8 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
     uint32_t *xs2 = smem + warp * words;          // two staging buffers of C::XS words
     int32_t *xf = (int32_t *)(xs2 + 2 * C::XS);
     int32_t *red = xf + C::XF;
-    int32_t *zs = red + C::RED;
-    int32_t *es = zs + C::ZS;
-    int32_t *wcache = es + C::ES + lane;          // stride 32: conflict-free
+    uint32_t *ezh = (uint32_t *)(red + C::RED);
+    int32_t *wcache = (int32_t *)(ezh + C::EZ) + lane;   // stride 32: conflict-free
 
     const int h = lane & 1;                   // frequency parity held by this lane
     const int task = lane >> 1;
@@ -246,7 +344,8 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
             }
             __syncwarp();
 
-            // outputs and RDE error of this polarisation
+            // outputs and RDE error of this polarisation; e z of each output as
+            // four balanced 12-bit limbs in f16 (the B operand of the gradient)
             for (int i = lane; i < SA; i += 32) {
                 int32_t a0 = 0, a1 = 0;
 #pragma unroll
@@ -262,36 +361,32 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                 const int64_t R = r2 < 6 * A2 ? 2 * A2 : (r2 < 14 * A2 ? 10 * A2 : 18 * A2);
                 if (valid && t >= ch.keep)
                     *(uint32_t *)(out + t * 4 + 2 * p) = ((uint32_t)z0 & 0xFFFFu) | ((uint32_t)z1 << 16);
-                zs[i] = valid ? z0 : 0;
-                zs[SA + i] = valid ? z1 : 0;
-                es[i] = valid ? (int32_t)(R - r2) : 0;
+                if (mu < 63) {
+                    const int32_t e = valid ? (int32_t)(R - r2) : 0;
+                    __half *col = (__half *)ezh + i;             // row 4 o + l, stride 2 EZ_ROW halves
+                    ez_limbs<2 * C::EZ_ROW>(mad_wide(e, z0, kLimbBias), col);
+                    ez_limbs<2 * C::EZ_ROW>(mad_wide(e, z1, kLimbBias), col + 8 * C::EZ_ROW);
+                }
             }
             __syncwarp();
 
-            // eq. (6): G[k] = sum_i e[i] z_S2[i] x_S1[t0 + i - k] for k = k0 .. k0 + 3,
-            // summed over the blocks of the update period
+            // eq. (6): G[k] = sum_i e[i] z_S2[i] x_S1[t0 + i - k], summed over the
+            // blocks of the update period
             const bool apply = !PER || ++in_period == period || blk + 1 == nblk;
             if (PER && apply) in_period = 0;
             if (mu < 63) {
-                // rolling window: w0..w3 = x_S1[t0 + i - k0 - kk], kk = 0..3, read
-                // as sign-extending byte loads of stream s1 from the staged words
-                const int8_t *xb = (const int8_t *)(xs + bb * SA + K - k0) + s1;
-                int32_t w1 = xb[-4], w2 = xb[-8], w3 = xb[-12];
-                const int32_t *zrow = zs + o * SA;
-#pragma unroll 4
-                for (int i = 0; i < SA; ++i) {
-                    const int32_t w0 = xb[4 * i];
-                    const int32_t e = es[i];
-                    const int32_t z = zrow[i];
-                    // |z w| <= 2^19: 32-bit product; e (z w) + acc in one wide multiply-add
-                    acc[0] = mad_wide(e, z * w0, acc[0]);
-                    acc[1] = mad_wide(e, z * w1, acc[1]);
-                    acc[2] = mad_wide(e, z * w2, acc[2]);
-                    acc[3] = mad_wide(e, z * w3, acc[3]);
-                    w3 = w2;
-                    w2 = w1;
-                    w1 = w0;
+                gradient_mma<C>(xs + bb * SA + K, ezh, red, lane);
+                __syncwarp();
+                // this lane's taps k0 .. k0 + 3: G = sum_limb c_limb 2^(12 limb)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int4 c4 = *(const int4 *)(red + (s1 * K + k0 + kk) * 8 + 4 * o);
+                    int64_t v = acc[kk] + c4.x;
+                    v = mad_wide(c4.y, 1 << 12, v);
+                    v = mad_wide(c4.z, 1 << 24, v);
+                    acc[kk] = v + ((int64_t)c4.w << 36);
                 }
+                __syncwarp();                             // gs is rewritten by the next block
                 if (apply) {
                     int32_t nv[4];
 #pragma unroll
