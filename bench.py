@@ -247,6 +247,7 @@ def run_fnt(args, rank, world, local_rank):
     S = 64 - L + 1
     plan = fnt.Plan(n_aeq=wl["n_aeq"], alpha_aeq=wl["alpha_aeq"], mu_shift=MU_SHIFT,
                     aeq_segment=wl["segment"], aeq_warmup=wl["warmup"], aeq_update_period=wl.get("period", 1))
+    plan.set_tensor_gradient(args.tensor_gradient)
     nsym = fnt.chain_nsym(n, L)
     x = torch.from_numpy(x_np).to(dev)
     out = torch.zeros((nsym, 4), dtype=torch.int16, device=dev)
@@ -368,6 +369,8 @@ def run_fnt(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload + ": " + wl["desc"], "aeq_update_period": wl.get("period", 1),
+                   "aeq_gradient": "tensor cores (exact f16 limbs, opt-in)" if args.tensor_gradient
+                   else "integer pipes (int64 multiply-add)",
                    "samples_per_step": n, "symbols_per_step": nsym,
                    "l2": "flushed between timed steps (256 MiB write outside the events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -643,6 +646,8 @@ def main(argv=None):
     ap.add_argument("--cpu-segments", type=int, default=128)
     ap.add_argument("--ref-segments", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tensor-gradient", action="store_true",
+                    help="cfg2 / cfg5: AEQ gradient on the tensor cores (bit-identical; off = integer path)")
     ap.add_argument("--aeq-period", type=int, default=1,
                     help="cfg2 / cfg5: AEQ blocks per tap update (1 = every block, as in eq. (6))")
     args = ap.parse_args(argv)

@@ -255,6 +255,15 @@ FNT_API fnt_status fnt_plan_set_launch(fnt_plan *plan, int32_t cdc_warps, int32_
  * piece is a latency-bound set of serial chains.) */
 FNT_API fnt_status fnt_plan_set_pipeline(fnt_plan *plan, int32_t chunks);
 
+/* on = 1: later AEQ launches of this plan compute the gradient of eq. (6) on the
+ * tensor cores instead of the integer pipes (default 0).  Results are
+ * bit-identical: e z (|e z| <= 2^46) is split into four balanced 12-bit limbs,
+ * which, like the 5-bit input, are exact in f16, and every per-block sum of
+ * limb x input products stays below 2^24, so the f32 accumulation is exact and
+ * the limb sums are recombined in int64.  Off by default because the paper's
+ * path is integer arithmetic throughout. */
+FNT_API fnt_status fnt_plan_set_tensor_gradient(fnt_plan *plan, int32_t on);
+
 /* ------------------------------------------------- allocation-free chain ---- */
 
 /* Largest frame (samples) and AEQ segment count fnt_cdc_aeq_run_noalloc takes. */

@@ -67,6 +67,7 @@ SIGNATURES = {
     "fnt_plan_destroy": (_I32, [_VP]),
     "fnt_plan_set_launch": (_I32, [_VP, _I32, _I32]),
     "fnt_plan_set_pipeline": (_I32, [_VP, _I32]),
+    "fnt_plan_set_tensor_gradient": (_I32, [_VP, _I32]),
     "fnt_op_counts_for": (_I32, [ctypes.POINTER(PlanDesc), _I32, ctypes.POINTER(OpCounts)]),
     "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
     "fnt_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
@@ -174,6 +175,10 @@ class Plan:
 
     def set_pipeline(self, chunks: int):
         check(lib().fnt_plan_set_pipeline(self.handle, chunks))
+
+    def set_tensor_gradient(self, on: bool):
+        """AEQ gradient on the tensor cores (exact; same results)."""
+        check(lib().fnt_plan_set_tensor_gradient(self.handle, int(bool(on))))
 
 
 class Frame:

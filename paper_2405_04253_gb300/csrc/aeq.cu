@@ -52,7 +52,8 @@ struct AeqCfg {
     static constexpr int RED = 16 * RED_ROW > GS ? 16 * RED_ROW : GS;  // per-task outputs, then GS
     static constexpr int KT = SA / 16;                       // k-steps of the gradient product
     static constexpr int EZ_ROW = SA / 2 + 4;                // f16 pairs per limb row; conflict-free
-    static constexpr int EZ = 8 * EZ_ROW;                    // e z limbs [o, limb][SA] as f16
+    static constexpr int EZH = 8 * EZ_ROW;                   // e z limbs [o, limb][SA] as f16
+    static constexpr int EZ = EZH > 3 * SA ? EZH : 3 * SA;   // ... or z [2][SA] and e [SA] as int32
     static constexpr int WORDS = 2 * XS + XF + RED + EZ;     // xs double-buffered
     static constexpr int WCACHE = 32 * M;                    // tap half-spectra [M][lane], P > 1 only
     static_assert(SA % 16 == 0 && (2 * XS + XF) % 4 == 0 && RED % 4 == 0 && WORDS % 4 == 0,
@@ -221,7 +222,9 @@ __device__ __forceinline__ void gradient_mma(const uint32_t *xw, const uint32_t 
 
 // PER: update period P > 1 (gradient summed over P blocks, tap spectra cached);
 // the P = 1 instance is the per-block update with no period bookkeeping.
-template <int NA, int64_t ALPHA, bool PER>
+// MMA: the gradient on the tensor cores (exact, opt-in); otherwise int32 x
+// int32 -> int64 multiply-adds on the integer pipes.
+template <int NA, int64_t ALPHA, bool PER, bool MMA>
 __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ frames,
                                                   const AeqChain *__restrict__ chains, int n_items,
                                                   AeqParams prm) {
@@ -239,6 +242,8 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
     int32_t *xf = (int32_t *)(xs2 + 2 * C::XS);
     int32_t *red = xf + C::XF;
     uint32_t *ezh = (uint32_t *)(red + C::RED);
+    int32_t *zs = (int32_t *)ezh;                 // integer gradient: z of both outputs, then e
+    int32_t *es = zs + 2 * SA;
     int32_t *wcache = (int32_t *)(ezh + C::EZ) + lane;   // stride 32: conflict-free
 
     const int h = lane & 1;                   // frequency parity held by this lane
@@ -361,11 +366,17 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                 const int64_t R = r2 < 6 * A2 ? 2 * A2 : (r2 < 14 * A2 ? 10 * A2 : 18 * A2);
                 if (valid && t >= ch.keep)
                     *(uint32_t *)(out + t * 4 + 2 * p) = ((uint32_t)z0 & 0xFFFFu) | ((uint32_t)z1 << 16);
-                if (mu < 63) {
-                    const int32_t e = valid ? (int32_t)(R - r2) : 0;
-                    __half *col = (__half *)ezh + i;             // row 4 o + l, stride 2 EZ_ROW halves
-                    ez_limbs<2 * C::EZ_ROW>(mad_wide(e, z0, kLimbBias), col);
-                    ez_limbs<2 * C::EZ_ROW>(mad_wide(e, z1, kLimbBias), col + 8 * C::EZ_ROW);
+                const int32_t e = valid ? (int32_t)(R - r2) : 0;
+                if constexpr (MMA) {
+                    if (mu < 63) {
+                        __half *col = (__half *)ezh + i;         // row 4 o + l, stride 2 EZ_ROW halves
+                        ez_limbs<2 * C::EZ_ROW>(mad_wide(e, z0, kLimbBias), col);
+                        ez_limbs<2 * C::EZ_ROW>(mad_wide(e, z1, kLimbBias), col + 8 * C::EZ_ROW);
+                    }
+                } else {
+                    zs[i] = valid ? z0 : 0;
+                    zs[SA + i] = valid ? z1 : 0;
+                    es[i] = e;
                 }
             }
             __syncwarp();
@@ -375,18 +386,40 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
             const bool apply = !PER || ++in_period == period || blk + 1 == nblk;
             if (PER && apply) in_period = 0;
             if (mu < 63) {
-                gradient_mma<C>(xs + bb * SA + K, ezh, red, lane);
-                __syncwarp();
-                // this lane's taps k0 .. k0 + 3: G = sum_limb c_limb 2^(12 limb)
+                if constexpr (MMA) {
+                    gradient_mma<C>(xs + bb * SA + K, ezh, red, lane);
+                    __syncwarp();
+                    // this lane's taps k0 .. k0 + 3: G = sum_limb c_limb 2^(12 limb)
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const int4 c4 = *(const int4 *)(red + (s1 * K + k0 + kk) * 8 + 4 * o);
-                    int64_t v = acc[kk] + c4.x;
-                    v = mad_wide(c4.y, 1 << 12, v);
-                    v = mad_wide(c4.z, 1 << 24, v);
-                    acc[kk] = v + ((int64_t)c4.w << 36);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int4 c4 = *(const int4 *)(red + (s1 * K + k0 + kk) * 8 + 4 * o);
+                        int64_t v = acc[kk] + c4.x;
+                        v = mad_wide(c4.y, 1 << 12, v);
+                        v = mad_wide(c4.z, 1 << 24, v);
+                        acc[kk] = v + ((int64_t)c4.w << 36);
+                    }
+                    __syncwarp();                         // gs is rewritten by the next block
+                } else {
+                    // taps k0 .. k0 + 3 over a rolling window w0..w3 = x_S1[t0 + i - k0 - kk],
+                    // read as sign-extending byte loads of stream s1 from the staged words
+                    const int8_t *xb = (const int8_t *)(xs + bb * SA + K - k0) + s1;
+                    int32_t w1 = xb[-4], w2 = xb[-8], w3 = xb[-12];
+                    const int32_t *zrow = zs + o * SA;
+#pragma unroll 4
+                    for (int i = 0; i < SA; ++i) {
+                        const int32_t w0 = xb[4 * i];
+                        const int32_t e = es[i];
+                        const int32_t z = zrow[i];
+                        // |z w| <= 2^19: 32-bit product; e (z w) + acc in one wide multiply-add
+                        acc[0] = mad_wide(e, z * w0, acc[0]);
+                        acc[1] = mad_wide(e, z * w1, acc[1]);
+                        acc[2] = mad_wide(e, z * w2, acc[2]);
+                        acc[3] = mad_wide(e, z * w3, acc[3]);
+                        w3 = w2;
+                        w2 = w1;
+                        w1 = w0;
+                    }
                 }
-                __syncwarp();                             // gs is rewritten by the next block
                 if (apply) {
                     int32_t nv[4];
 #pragma unroll
@@ -436,18 +469,41 @@ size_t aeq_smem_bytes(int na, int warps, int period) {
     return (size_t)warps * words * sizeof(uint32_t);
 }
 
-template <int NA, int64_t ALPHA, bool PER>
+template <int NA, int64_t ALPHA, bool PER, bool MMA>
 static cudaError_t aeq_configure_one() {
-    return cudaFuncSetAttribute(aeq_kernel<NA, ALPHA, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(aeq_kernel<NA, ALPHA, PER, MMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)aeq_smem_bytes(NA, 4, PER ? 2 : 1));
 }
 
-cudaError_t aeq_configure() {
-    cudaError_t e = aeq_configure_one<64, 4080, false>();
-    if (e == cudaSuccess) e = aeq_configure_one<64, 4080, true>();
-    if (e == cudaSuccess) e = aeq_configure_one<32, 2, false>();
-    if (e == cudaSuccess) e = aeq_configure_one<32, 2, true>();
+template <int NA, int64_t ALPHA>
+static cudaError_t aeq_configure_n() {
+    cudaError_t e = aeq_configure_one<NA, ALPHA, false, false>();
+    if (e == cudaSuccess) e = aeq_configure_one<NA, ALPHA, true, false>();
+    if (e == cudaSuccess) e = aeq_configure_one<NA, ALPHA, false, true>();
+    if (e == cudaSuccess) e = aeq_configure_one<NA, ALPHA, true, true>();
     return e;
+}
+
+cudaError_t aeq_configure() {
+    cudaError_t e = aeq_configure_n<64, 4080>();
+    return e == cudaSuccess ? aeq_configure_n<32, 2>() : e;
+}
+
+template <int NA, int64_t ALPHA>
+static void aeq_launch_n(dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const DevFrame *frames,
+                         const AeqChain *chains, int n_items, AeqParams prm, bool mma) {
+    const bool per = prm.period > 1;
+    if (mma) {
+        if (per)
+            aeq_kernel<NA, ALPHA, true, true><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+        else
+            aeq_kernel<NA, ALPHA, false, true><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+    } else {
+        if (per)
+            aeq_kernel<NA, ALPHA, true, false><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+        else
+            aeq_kernel<NA, ALPHA, false, false><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+    }
 }
 
 // Work items are (chain, polarisation) pairs: 2 per chain.
@@ -458,15 +514,10 @@ cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, i
     const size_t smem = aeq_smem_bytes(na, warps, prm.period);
     const int n_items = 2 * n_chains;
     if (grid <= 0) grid = (n_items + warps - 1) / warps;
-    const bool per = prm.period > 1;
-    if (na == 64 && per)
-        aeq_kernel<64, 4080, true><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
-    else if (na == 64)
-        aeq_kernel<64, 4080, false><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
-    else if (per)
-        aeq_kernel<32, 2, true><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+    if (na == 64)
+        aeq_launch_n<64, 4080>(dim3(grid), block, smem, stream, frames, chains, n_items, prm, prm.tensor_gradient != 0);
     else
-        aeq_kernel<32, 2, false><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+        aeq_launch_n<32, 2>(dim3(grid), block, smem, stream, frames, chains, n_items, prm, prm.tensor_gradient != 0);
     return cudaGetLastError();
 }
 

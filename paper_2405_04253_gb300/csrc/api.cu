@@ -206,6 +206,13 @@ extern "C" fnt_status fnt_plan_set_pipeline(fnt_plan *p, int32_t chunks) {
     return FNT_OK;
 }
 
+extern "C" fnt_status fnt_plan_set_tensor_gradient(fnt_plan *p, int32_t on) {
+    if (!p) return fail(FNT_ERR_INVALID, "null plan");
+    if (on != 0 && on != 1) return fail(FNT_ERR_INVALID, "tensor_gradient must be 0 or 1");
+    p->tensor_gradient = on;
+    return FNT_OK;
+}
+
 // ---------------------------------------------------------- work building ---
 
 namespace fnt {
@@ -440,7 +447,7 @@ static fnt_status launch_aeq_range(const fnt_plan *p, const Work &w, const char 
                                    cudaStream_t stream) {
     if (c1 <= c0) return FNT_OK;
     const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
-    AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d)};
+    AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d), p->tensor_gradient};
     cudaError_t e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(dev + w.off_chains) + c0, c1 - c0, prm,
                                p->aeq_warps, 0, stream);
     return e == cudaSuccess ? FNT_OK : cuda_fail(e, "aeq kernel launch");

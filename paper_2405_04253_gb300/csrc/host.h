@@ -18,6 +18,7 @@ struct fnt_plan {
     int cdc_warps = 4;
     int aeq_warps = 2;
     int chunks = 1;              // pipelined chunks of prepared chain batches (1 = off)
+    int tensor_gradient = 0;     // AEQ gradient on the tensor cores (opt-in, same results)
 };
 
 namespace fnt {

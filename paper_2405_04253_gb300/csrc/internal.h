@@ -48,6 +48,7 @@ struct AeqParams {
     int32_t mu_shift;
     int32_t rde_a;
     int32_t period;       // blocks per tap update, >= 1
+    int32_t tensor_gradient;  // 1: gradient on the tensor cores (same results)
 };
 
 constexpr int kMaxUpdatePeriod = 64;   // keeps the summed int64 gradient exact

@@ -119,31 +119,46 @@ def run_aeq(plan, x, T=None):
     return out.cpu().numpy(), (None if st is None else st.cpu().numpy())
 
 
+@pytest.mark.parametrize("tensor", [False, True])
 @pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
 @pytest.mark.parametrize("n,mu", [(1000, 8), (333, 12), (16, 8), (5, 8), (2000, 63), (4096 + 3, 6)])
-def test_aeq_matches_oracle(orc, na, alpha, n, mu):
+def test_aeq_matches_oracle(orc, na, alpha, n, mu, tensor):
     rng = np.random.default_rng(na * 1000 + n + mu)
     x = rng.integers(-16, 16, (n, 4)).astype(np.int8)
     T0 = orc.aeq_init_taps(16, 2048)
     T0 = T0 + rng.integers(-(1 << 20), 1 << 20, T0.shape).astype(np.int32)
     plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=mu, rde_a=64)
+    plan.set_tensor_gradient(tensor)
     got, Tg = run_aeq(plan, x, T0)
     ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=mu, rde_a=64)
     assert np.array_equal(got, ref)
     assert np.array_equal(Tg, Tr)
 
 
+@pytest.mark.parametrize("tensor", [False, True])
 @pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
-def test_aeq_extreme_taps(orc, na, alpha):
+def test_aeq_extreme_taps(orc, na, alpha, tensor):
+    """Saturated outputs (|z| = 32767 / 32768), |e| near 2^31 and inputs at both
+    ends of the 5-bit range: the largest e z the gradient can see."""
     rng = np.random.default_rng(3)
     x = np.full((700, 4), -16, dtype=np.int8)
     x[::3] = 15
     W = rng.choice([-8192, 8191, -1, 0, 127, -128], size=(4, 4, 16)).astype(np.int64)
-    T0 = (W << 16).astype(np.int32)
-    plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=30, rde_a=4096)
-    got, Tg = run_aeq(plan, x, T0)
-    ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=30, rde_a=4096)
-    assert np.array_equal(got, ref) and np.array_equal(Tg, Tr)
+    cases = [(W << 16).astype(np.int32)]
+    xs = [x]
+    x2 = np.full((700, 4), -16, dtype=np.int8)
+    x2[::7] = 15
+    for wv in (8191, -8192):                       # every tap at an end of the range
+        cases.append(np.full((4, 4, 16), wv << 16, dtype=np.int64).astype(np.int32))
+        xs.append(x2)
+    for xi, T0 in zip(xs, cases):
+        for mu, a in ((30, 4096), (40, 1)):
+            plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=mu, rde_a=a)
+            plan.set_tensor_gradient(tensor)
+            got, Tg = run_aeq(plan, xi, T0)
+            ref, Tr = orc.aeq(xi, T0, na, alpha, mu_shift=mu, rde_a=a)
+            assert np.array_equal(got, ref) and np.array_equal(Tg, Tr)
+    assert np.abs(got.astype(np.int64)).max() >= 32767          # saturated outputs were covered
 
 
 def test_aeq_no_state_uses_plan_init(orc):
@@ -173,9 +188,10 @@ def test_aeq_segmented_matches_oracle(orc, na, alpha):
     assert np.array_equal(got2, ref2)
 
 
+@pytest.mark.parametrize("tensor", [False, True])
 @pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
 @pytest.mark.parametrize("period,n", [(2, 1000), (3, 333), (5, 4099), (64, 5000), (64, 700), (4, 16)])
-def test_aeq_update_period_matches_oracle(orc, na, alpha, period, n):
+def test_aeq_update_period_matches_oracle(orc, na, alpha, period, n, tensor):
     """Update period P: the summed gradient of P blocks is applied after every
     P-th block and the last; the taps (and their cached spectra) are fixed in
     between."""
@@ -183,6 +199,7 @@ def test_aeq_update_period_matches_oracle(orc, na, alpha, period, n):
     x = rng.integers(-16, 16, (n, 4)).astype(np.int8)
     T0 = orc.aeq_init_taps(16, 2048) + rng.integers(-(1 << 20), 1 << 20, (4, 4, 16)).astype(np.int32)
     plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=12, aeq_update_period=period)
+    plan.set_tensor_gradient(tensor)
     got, Tg = run_aeq(plan, x, T0)
     ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=12, rde_a=64, period=period)
     assert np.array_equal(got, ref)
@@ -328,6 +345,16 @@ def test_chain_full_size_cfg2_sampled_segments(orc):
     assert bp.kernel_count() > 2
     assert np.array_equal(out2.cpu().numpy(), got)
     assert torch.equal(st2, st)
+    # and so does the tensor-core gradient
+    st3 = dev(T0)
+    out3 = i16((nsym, 4))
+    plan.set_pipeline(1)
+    plan.set_tensor_gradient(True)
+    bt = F.Batch(plan, [F.Frame(xd, out3, f.taps, st3)], F.OP_CHAIN, use_graph=True)
+    bt.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(out3.cpu().numpy(), got)
+    assert torch.equal(st3, st)
     n_seg = (nsym + 1023) // 1024
     rng = np.random.default_rng(2)
     segs = sorted({0, 1, n_seg // 2, n_seg - 2, n_seg - 1, *rng.integers(0, n_seg, 15).tolist()})
