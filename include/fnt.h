@@ -255,6 +255,12 @@ FNT_API fnt_status fnt_plan_set_launch(fnt_plan *plan, int32_t cdc_warps, int32_
  * piece is a latency-bound set of serial chains.) */
 FNT_API fnt_status fnt_plan_set_pipeline(fnt_plan *plan, int32_t chunks);
 
+/* CDC work items created after this call cover 32 overlap-save blocks of one
+ * polarisation (pols = 1) or of both polarisations of a PDM frame (pols = 2);
+ * 0 (default) picks 2 when the work fills the GPU at least twice over and 1
+ * otherwise.  Results do not depend on it. */
+FNT_API fnt_status fnt_plan_set_cdc_items(fnt_plan *plan, int32_t pols);
+
 /* on = 1: later AEQ launches of this plan compute the gradient of eq. (6) on the
  * tensor cores instead of the integer pipes (default 0).  Results are
  * bit-identical: e z (|e z| <= 2^46) is split into four balanced 12-bit limbs,

@@ -68,6 +68,7 @@ SIGNATURES = {
     "fnt_plan_set_launch": (_I32, [_VP, _I32, _I32]),
     "fnt_plan_set_pipeline": (_I32, [_VP, _I32]),
     "fnt_plan_set_tensor_gradient": (_I32, [_VP, _I32]),
+    "fnt_plan_set_cdc_items": (_I32, [_VP, _I32]),
     "fnt_op_counts_for": (_I32, [ctypes.POINTER(PlanDesc), _I32, ctypes.POINTER(OpCounts)]),
     "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
     "fnt_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
@@ -175,6 +176,10 @@ class Plan:
 
     def set_pipeline(self, chunks: int):
         check(lib().fnt_plan_set_pipeline(self.handle, chunks))
+
+    def set_cdc_items(self, pols: int):
+        """CDC items of one (1) or both (2) polarisations; 0 = automatic."""
+        check(lib().fnt_plan_set_cdc_items(self.handle, pols))
 
     def set_tensor_gradient(self, on: bool):
         """AEQ gradient on the tensor cores (exact; same results)."""

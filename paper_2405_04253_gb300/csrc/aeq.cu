@@ -43,6 +43,11 @@ struct AeqCfg {
     static constexpr int M = NA / 2;                         // values per lane
     static constexpr int SA = NA - K;                        // symbols per block
     static constexpr int PRE = 8;                            // blocks per input-spectrum batch
+    // code-size choices: at N = 32 the fully unrolled forms are small and
+    // faster; at N = 64 one N/2-point code copy run twice and a partly unrolled
+    // gradient keep the kernel inside the instruction cache
+    static constexpr bool FULL_INPUT = NA == 32;             // input spectra as one N-point transform
+    static constexpr int GRAD_UNROLL = NA == 32 ? NA - kAeqK : 4;
     static constexpr int XS = PRE * SA + K;                  // staged input symbols (char4 words)
     static constexpr int HALF = M + 1;                       // padded half row
     static constexpr int XF_ROW = 2 * HALF + 1;              // conflict-free: rows 3 banks apart
@@ -289,19 +294,32 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                                        lane);
                 {
                     // N-point spectrum of input sq for block bq, N^-1 folded in, as
-                    // its even and odd halves: X[2k'+hh] = FNT_{N/2, alpha^2} of
-                    // a_j + a_{j+N/2} (hh = 0) or (a_j - a_{j+N/2}) alpha^j (hh = 1),
-                    // in bit-reversed order -- one N/2-point code copy, two trips.
+                    // its even and odd halves in bit-reversed order: X[2k'+hh].
                     const int bq = lane >> 2, sq = lane & 3;
                     const uint32_t *xw = xs + bq * SA;
                     int32_t *row = xf + (bq * 4 + sq) * C::XF_ROW;
-#pragma unroll 1
-                    for (int hh = 0; hh < 2; ++hh) {
-                        int32_t y[M];
-                        SplitInput<NA, ALPHA, 0>::run(y, xw, 8 * sq, hh != 0);
-                        fnt_fwd<M, C::ALPHA2, 17>(y);
+                    if constexpr (C::FULL_INPUT) {
+                        // one N-point transform: register hh M + j holds X[2 bitrev_M(j) + hh]
+                        int32_t xv[NA];
 #pragma unroll
-                        for (int j = 0; j < M; ++j) row[hh * C::HALF + j] = rhoc(rho(rhoc(y[j]) * C::NINV));
+                        for (int j = 0; j < NA; ++j) xv[j] = sx8(xw[j], 8 * sq);
+                        fnt_fwd<NA, ALPHA, 5>(xv);                   // |x| <= 16
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+                            for (int j = 0; j < M; ++j)
+                                row[hh * C::HALF + j] = rhoc(rho(rhoc(xv[hh * M + j]) * C::NINV));
+                    } else {
+                        // X[2k'+hh] = FNT_{N/2, alpha^2} of a_j + a_{j+N/2} (hh = 0) or
+                        // (a_j - a_{j+N/2}) alpha^j (hh = 1): one N/2-point code copy, two trips
+#pragma unroll 1
+                        for (int hh = 0; hh < 2; ++hh) {
+                            int32_t y[M];
+                            SplitInput<NA, ALPHA, 0>::run(y, xw, 8 * sq, hh != 0);
+                            fnt_fwd<M, C::ALPHA2, 17>(y);
+#pragma unroll
+                            for (int j = 0; j < M; ++j) row[hh * C::HALF + j] = rhoc(rho(rhoc(y[j]) * C::NINV));
+                        }
                     }
                 }
                 __syncwarp();
@@ -405,7 +423,7 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                     const int8_t *xb = (const int8_t *)(xs + bb * SA + K - k0) + s1;
                     int32_t w1 = xb[-4], w2 = xb[-8], w3 = xb[-12];
                     const int32_t *zrow = zs + o * SA;
-#pragma unroll 4
+#pragma unroll C::GRAD_UNROLL
                     for (int i = 0; i < SA; ++i) {
                         const int32_t w0 = xb[4 * i];
                         const int32_t e = es[i];

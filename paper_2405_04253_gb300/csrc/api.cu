@@ -206,6 +206,13 @@ extern "C" fnt_status fnt_plan_set_pipeline(fnt_plan *p, int32_t chunks) {
     return FNT_OK;
 }
 
+extern "C" fnt_status fnt_plan_set_cdc_items(fnt_plan *p, int32_t pols) {
+    if (!p) return fail(FNT_ERR_INVALID, "null plan");
+    if (pols < 0 || pols > 2) return fail(FNT_ERR_INVALID, "pols per CDC item must be 0, 1 or 2");
+    p->cdc_pols_per_item = pols;
+    return FNT_OK;
+}
+
 extern "C" fnt_status fnt_plan_set_tensor_gradient(fnt_plan *p, int32_t on) {
     if (!p) return fail(FNT_ERR_INVALID, "null plan");
     if (on != 0 && on != 1) return fail(FNT_ERR_INVALID, "tensor_gradient must be 0 or 1");
@@ -269,11 +276,32 @@ static fnt_status make_frame(const fnt_plan *p, const fnt_frame &f, int op, int 
     return FNT_OK;
 }
 
-static void add_cdc_items(const DevFrame &df, int fi, std::vector<int4> &items) {
+// CDC items of one frame: 32 blocks of one polarisation each (w = pol), or, with
+// `both`, of both polarisations of a PDM frame (w = 2: one window fill and one
+// tap-spectrum set serve the two).
+static void add_cdc_items(const DevFrame &df, int fi, bool both, std::vector<int4> &items) {
     const int64_t nblk = (df.n + df.S - 1) / df.S;
-    for (int64_t b = 0; b < nblk; b += kBlocksPerItem)
-        for (int p = 0; p < df.n_pol; ++p)
-            items.push_back(make_int4(fi, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), p));
+    for (int64_t b = 0; b < nblk; b += kBlocksPerItem) {
+        const int nb = (int)std::min<int64_t>(kBlocksPerItem, nblk - b);
+        if (both && df.n_pol == 2) {
+            items.push_back(make_int4(fi, (int)b, nb, 2));
+        } else {
+            for (int p = 0; p < df.n_pol; ++p) items.push_back(make_int4(fi, (int)b, nb, p));
+        }
+    }
+}
+
+// Whether the CDC items of this work take both polarisations at once.  Per-
+// polarisation items double the warps (better for work that does not fill the
+// GPU twice over); two-polarisation items halve the window fills and the tap
+// spectra per block (better once there is work for several waves).
+static bool cdc_items_both(const fnt_plan *p, const Work &w) {
+    if (p->cdc_pols_per_item != 0) return p->cdc_pols_per_item == 2;
+    int64_t items = 0;
+    for (const DevFrame &df : w.frames)
+        if (df.n_pol == 2) items += ((df.n + df.S - 1) / df.S + kBlocksPerItem - 1) / kBlocksPerItem;
+    const int64_t resident = (int64_t)p->n_sm * kCdcCtasPerSm * p->cdc_warps;
+    return items >= 2 * resident;
 }
 
 // AEQ runs of one frame.  Unsegmented: one chain that reads and writes the
@@ -339,9 +367,11 @@ fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work 
     if (op == FNT_OP_CHAIN)
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int c) { return w.frames[a].n_sym > w.frames[c].n_sym; });
+    const bool both = op != FNT_OP_AEQ && cdc_items_both(p, w);
+    w.cdc_both = both;
     for (int i : order) {
         const int first_item = (int)w.items.size();
-        if (op != FNT_OP_AEQ) add_cdc_items(w.frames[i], i, w.items);
+        if (op != FNT_OP_AEQ) add_cdc_items(w.frames[i], i, both, w.items);
         if (op != FNT_OP_CDC) {
             const size_t c0 = w.chains.size();
             add_aeq_chains(p, w.frames[i], i, p->d_init, w);
@@ -349,8 +379,9 @@ fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work 
                 const DevFrame &df = w.frames[i];
                 // last 2-sps sample the chain reads, and the CDC item that produces it
                 const int64_t t_last = 2 * (w.chains[c].end - 1) + df.phase;
+                const int per = both && df.n_pol == 2 ? 1 : df.n_pol;     // items per 32 blocks
                 w.chains[c].need_item =
-                    op == FNT_OP_CHAIN ? first_item + (int)(t_last / df.S / kBlocksPerItem) * df.n_pol + df.n_pol - 1 : 0;
+                    op == FNT_OP_CHAIN ? first_item + (int)(t_last / df.S / kBlocksPerItem) * per + per - 1 : 0;
             }
         }
     }
@@ -429,8 +460,8 @@ static fnt_status launch_cdc_range(const fnt_plan *p, const Work &w, const char 
     const int nw = p->cdc_warps;
     const int n = i1 - i0;
     const int grid = std::min((n + nw - 1) / nw, p->n_sm * 64);
-    cudaError_t e = cdc_launch(frames, (const int4 *)(dev + w.off_items) + i0, n, w.op == FNT_OP_CHAIN, nw, grid,
-                               stream);
+    cudaError_t e = cdc_launch(frames, (const int4 *)(dev + w.off_items) + i0, n, w.op == FNT_OP_CHAIN, w.cdc_both,
+                               nw, grid, stream);
     return e == cudaSuccess ? FNT_OK : cuda_fail(e, "cdc kernel launch");
 }
 

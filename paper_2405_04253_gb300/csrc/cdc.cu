@@ -90,8 +90,12 @@ __device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, cons
     }
 }
 
-template <bool CHAIN>
-__global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict__ frames,
+// BOTH: items may cover both polarisations of a PDM frame (item.w = 2); such a
+// warp runs the two blocks of each lane back to back from one window fill and
+// one tap-spectrum set, and stores each symbol's 4-byte word at once.  That
+// form needs more registers, so it runs 2 CTAs per SM instead of 3.
+template <bool CHAIN, bool BOTH>
+__global__ void __launch_bounds__(128, BOTH ? 2 : 3) cdc_kernel(const DevFrame *__restrict__ frames,
                                                      const int4 *__restrict__ items, int n_items) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int32_t s_pow[kN];
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict_
         const DevFrame &fr = frames[item.x];
         const int64_t b0 = item.y;
         const int nb = item.z;
-        const int pol = item.w;                       // polarisation this warp computes
+        const int pol = item.w;                       // polarisation this warp computes, 2 = both
         const int S = fr.S;
         const int L = fr.L;
         const int npol = fr.n_pol;
@@ -167,7 +171,16 @@ __global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict_
         }
         __syncwarp();
 
-        cdc_block(win, o0, hs, lane, 16 * pol);
+        // item.w = 2: both polarisations from the same windows and tap spectra;
+        // polarisation 1's results overwrite the lane's own window column
+        const bool two = BOTH && pol == 2;
+        if constexpr (BOTH) {
+            const int p_first = two ? 0 : pol, p_end = two ? 2 : pol + 1;
+#pragma unroll 1
+            for (int pp = p_first; pp < p_end; ++pp) cdc_block(win, pp > p_first ? win : o0, hs, lane, 16 * pp);
+        } else {
+            cdc_block(win, o0, hs, lane, 16 * pol);
+        }
         __syncwarp();
 
         if (!CHAIN) {
@@ -179,7 +192,10 @@ __global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict_
                     const int64_t t = (b0 + l) * S + jj;
                     if (jj < S && t < n) {
                         const int pos = (kN - S + jj) * kRow + l;
-                        *(uint32_t *)(out + (t * npol + pol) * 2) = o0[pos];
+                        if (two)
+                            *(uint2 *)(out + t * 4) = make_uint2(o0[pos], win[pos]);
+                        else
+                            *(uint32_t *)(out + (t * npol + pol) * 2) = o0[pos];
                     }
                 }
             }
@@ -187,18 +203,26 @@ __global__ void __launch_bounds__(128, 3) cdc_kernel(const DevFrame *__restrict_
             // requantise to 5 bits and keep times t = phase (mod 2)
             const int sft = fr.shift;
             const int32_t rnd = sft > 0 ? (1 << (sft - 1)) : 0;
-            uint16_t *xa = (uint16_t *)fr.aeq_in;
             for (int l = 0; l < nb; ++l) {
                 const int64_t t0 = (b0 + l) * S;
                 const int jj = (int)((t0 - fr.phase) & 1) + 2 * lane;
                 const int64_t t = t0 + jj;
                 if (jj < S && t < n) {
                     const int pos = (kN - S + jj) * kRow + l;
+                    const int64_t sym = (t - fr.phase) >> 1;
                     const uint32_t w0 = o0[pos];
-                    const int32_t c0 = sat5(((int32_t)(int16_t)(w0 & 0xFFFF) + rnd) >> sft);
-                    const int32_t c1 = sat5((((int32_t)w0 >> 16) + rnd) >> sft);
-                    // this polarisation's two bytes (I, Q) of the symbol's 4-byte word
-                    xa[2 * ((t - fr.phase) >> 1) + pol] = (uint16_t)((c0 & 0xFF) | ((c1 & 0xFF) << 8));
+                    const uint32_t q0 = (uint32_t)(sat5(((int32_t)(int16_t)(w0 & 0xFFFF) + rnd) >> sft) & 0xFF) |
+                                        ((uint32_t)(sat5((((int32_t)w0 >> 16) + rnd) >> sft) & 0xFF) << 8);
+                    if (two) {
+                        // the symbol's whole 4-byte word (XI, XQ, YI, YQ)
+                        const uint32_t w1 = win[pos];
+                        const uint32_t q1 = (uint32_t)(sat5(((int32_t)(int16_t)(w1 & 0xFFFF) + rnd) >> sft) & 0xFF) |
+                                            ((uint32_t)(sat5((((int32_t)w1 >> 16) + rnd) >> sft) & 0xFF) << 8);
+                        ((uint32_t *)fr.aeq_in)[sym] = q0 | (q1 << 16);
+                    } else {
+                        // this polarisation's two bytes (I, Q) of the symbol's word
+                        ((uint16_t *)fr.aeq_in)[2 * sym + pol] = (uint16_t)q0;
+                    }
                 }
             }
         }
@@ -216,22 +240,30 @@ int cdc_mults_per_block() { return 2 * kN; }
 int cdc_butterflies_per_block() { return 4 * (kN / 2) * 6; }
 
 cudaError_t cdc_configure() {
-    const size_t max_smem = cdc_smem_bytes(8);
-    cudaError_t e = cudaFuncSetAttribute(cdc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)max_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(cdc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    const int max_smem = (int)cdc_smem_bytes(8);
+    cudaError_t e = cudaFuncSetAttribute(cdc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cdc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cdc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cdc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    return e;
 }
 
-cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, int warps,
+cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, bool both, int warps,
                        int grid, cudaStream_t stream) {
     if (n_items <= 0) return cudaSuccess;
     const dim3 block(32 * warps);
     const size_t smem = cdc_smem_bytes(warps);
-    if (chain)
-        cdc_kernel<true><<<grid, block, smem, stream>>>(frames, items, n_items);
+    if (chain && both)
+        cdc_kernel<true, true><<<grid, block, smem, stream>>>(frames, items, n_items);
+    else if (chain)
+        cdc_kernel<true, false><<<grid, block, smem, stream>>>(frames, items, n_items);
+    else if (both)
+        cdc_kernel<false, true><<<grid, block, smem, stream>>>(frames, items, n_items);
     else
-        cdc_kernel<false><<<grid, block, smem, stream>>>(frames, items, n_items);
+        cdc_kernel<false, false><<<grid, block, smem, stream>>>(frames, items, n_items);
     return cudaGetLastError();
 }
 

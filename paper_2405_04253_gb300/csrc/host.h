@@ -19,6 +19,7 @@ struct fnt_plan {
     int aeq_warps = 2;
     int chunks = 1;              // pipelined chunks of prepared chain batches (1 = off)
     int tensor_gradient = 0;     // AEQ gradient on the tensor cores (opt-in, same results)
+    int cdc_pols_per_item = 0;   // CDC items: 0 auto, 1 one polarisation, 2 both
 };
 
 namespace fnt {
@@ -33,6 +34,7 @@ int64_t chain_nsym(int64_t n, int phase);
 // Work lists of one call or prepared batch.
 struct Work {
     int op = 0;
+    bool cdc_both = false;            // CDC items may cover both polarisations (item.w = 2)
     std::vector<DevFrame> frames;
     std::vector<int4> items;          // CDC: (frame, first block, blocks)
     std::vector<AeqChain> chains;     // AEQ runs, longest first
@@ -60,12 +62,13 @@ fnt_status launch_pipelined(const fnt_plan *p, const Work &w, const char *dev, c
 int work_kernel_count(const Work &w);
 
 // kernels
+constexpr int kCdcCtasPerSm = 3;     // cdc_kernel's __launch_bounds__ minimum
 size_t cdc_smem_bytes(int warps);
 int cdc_mults_per_block();
 int cdc_butterflies_per_block();
 int aeq_mults_per_block(int na);
 cudaError_t cdc_configure();
-cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, int warps, int grid,
+cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, bool both, int warps, int grid,
                        cudaStream_t stream);
 size_t aeq_smem_bytes(int na, int warps, int period);
 cudaError_t aeq_configure();

@@ -160,7 +160,7 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
 
     const DevFrame *frames = (const DevFrame *)(base + kOffFrame);
     const int nw = p->cdc_warps;
-    e = cdc_launch(frames, (const int4 *)(base + kOffItems), n_items, true, nw,
+    e = cdc_launch(frames, (const int4 *)(base + kOffItems), n_items, true, false, nw,
                    std::min((n_items + nw - 1) / nw, p->n_sm * 64), stream);
     if (e != cudaSuccess) return cuda_fail(e, "noalloc: cdc kernel launch");
     if (nc > 0) {

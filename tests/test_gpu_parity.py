@@ -75,9 +75,12 @@ def test_cdc_synthetic_config1(orc):
     assert np.array_equal(got, orc.cdc(f.x, f.taps))
 
 
-def test_cdc_batch_of_mixed_frames(orc):
+@pytest.mark.parametrize("pols", [0, 1, 2])
+def test_cdc_batch_of_mixed_frames(orc, pols):
+    """Items of one or of both polarisations (single-pol frames always take one)."""
     rng = np.random.default_rng(77)
     plan = F.Plan()
+    plan.set_cdc_items(pols)
     frames, refs = [], []
     for i in range(9):
         n = int(rng.integers(0, 9000))
@@ -345,10 +348,11 @@ def test_chain_full_size_cfg2_sampled_segments(orc):
     assert bp.kernel_count() > 2
     assert np.array_equal(out2.cpu().numpy(), got)
     assert torch.equal(st2, st)
-    # and so does the tensor-core gradient
+    # and so do two-polarisation CDC items with the tensor-core gradient
     st3 = dev(T0)
     out3 = i16((nsym, 4))
     plan.set_pipeline(1)
+    plan.set_cdc_items(2)
     plan.set_tensor_gradient(True)
     bt = F.Batch(plan, [F.Frame(xd, out3, f.taps, st3)], F.OP_CHAIN, use_graph=True)
     bt.launch()
@@ -377,19 +381,20 @@ def test_pipelined_batch_equals_oracle_and_unpipelined(orc):
         frames_np.append((rng.integers(-16, 16, (n, 2, 2)).astype(np.int8),
                           rng.integers(-32, 32, (L, 2)).astype(np.int8)))
     outs = {}
-    for chunks, graph in [(4, True), (3, False), (1, False)]:
+    for chunks, graph, pols in [(4, True, 1), (3, False, 2), (1, False, 0), (5, True, 2)]:
         plan = F.Plan(mu_shift=9)
         plan.set_pipeline(chunks)
+        plan.set_cdc_items(pols)
         frames = [F.Frame(dev(x), i16((F.chain_nsym(x.shape[0], t.shape[0]), 4)), t) for x, t in frames_np]
         b = F.Batch(plan, frames, F.OP_CHAIN, use_graph=graph)
         b.launch()
         b.launch()
         torch.cuda.synchronize()
         outs[chunks] = [fr.out.cpu().numpy() for fr in frames]
-        if chunks == 4:
+        if chunks > 1 and graph:
             assert b.kernel_count() > 2
-    for a, b_, c in zip(outs[4], outs[3], outs[1]):
-        assert np.array_equal(a, c) and np.array_equal(b_, c)
+    for a, b_, c, d in zip(outs[4], outs[3], outs[1], outs[5]):
+        assert np.array_equal(a, c) and np.array_equal(b_, c) and np.array_equal(d, c)
     for i in (0, 7, 39):
         ref, _ = orc.chain(frames_np[i][0], frames_np[i][1], orc.ChainParams(mu_shift=9))
         assert np.array_equal(outs[4][i], ref)
