@@ -6,8 +6,8 @@ requantise + resample, FNT-AEQ with RDE adaptation) over one batch of synthetic
 input already resident in device memory.  Default workload: one PDM-16QAM
 stream, 40 GBaud at 2 samples/symbol, 2^20 symbols per polarisation, 75 km
 (17 CD taps, 6 bit), 5-bit I/Q, AEQ 4x4 RV-MIMO at N = 64 / radix 4080 in
-segments of 1024 symbols with 48 warm-up symbols (one AEQ block, so the
-first kept output has its full 16-tap history), every segment starting from
+segments of 864 symbols (18 AEQ blocks) with 48 warm-up symbols (one block,
+so the first kept output has its full 16-tap history), every segment starting from
 the tap state the previous step ended with (a stream processed step by step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fnt|reference]
@@ -42,10 +42,11 @@ UNIT = "Gsamples/s"
 # ---------------------------------------------------------------- workload ----
 
 WORKLOADS = {
-    "cfg2": dict(n_sym=1 << 20, km=75.0, n_aeq=64, alpha_aeq=4080, segment=1024, warmup=48,
+    "cfg2": dict(n_sym=1 << 20, km=75.0, n_aeq=64, alpha_aeq=4080, segment=864, warmup=48,
                  desc="PDM-16QAM 40 GBaud 2 sps, 2^20 symbols/pol (2^21 samples), 75 km, 17 CD taps (6 bit), "
                       "5-bit I/Q, FNT-CDC N=64 alpha=4080 S=48 + FNT-AEQ 4x4 RV-MIMO N=64 alpha=4080 K=16, "
-                      "AEQ segments of 1024 symbols + 48 warm-up (one block) starting from the stream's carried taps"),
+                      "AEQ segments of 864 symbols (18 blocks) + 48 warm-up (one block) starting from the stream's "
+                      "carried taps"),
     "cfg5": dict(n_sym=1 << 26, km=80.0, n_aeq=32, alpha_aeq=2, segment=1 << 16, warmup=1 << 12,
                  desc="PDM bandwidth stress, one stream of 2^27 samples/pol (a generated 2^23-sample stretch "
                       "repeated), 80 km, 19 CD taps, FNT-AEQ N=32 alpha=2, segments 2^16 + 2^12 warm-up from "
@@ -227,6 +228,8 @@ def _segments(x_np, taps, wl, n_seg):
     L = taps.shape[0]
     nsym = (x_np.shape[0] - (((L - 1) // 2) & 1) + 1) // 2
     total = math.ceil(nsym / wl["segment"])
+    if n_seg <= 0 or n_seg > total:
+        n_seg = total                            # every segment: the whole step
     return sorted({int(i * total / n_seg) for i in range(n_seg)}), total
 
 
@@ -402,7 +405,7 @@ def init_taps():
 def cpu_baseline(x_np, taps, wl, out_dev=None, n_seg=96, procs=None, T0=None):
     """The oracle as it stands on a bounded sample: n_seg AEQ segments spread
     over the stream, in a spawn pool over the host cores."""
-    procs = procs or min(os.cpu_count() or 1, n_seg)
+    procs = procs or min(os.cpu_count() or 1, n_seg if n_seg > 0 else os.cpu_count() or 1)
     segs, total = _segments(x_np, taps, wl, n_seg)
     pool = OraclePool(x_np, taps, _prm_kw(wl), procs, init_taps() if T0 is None else T0)
     try:
@@ -643,7 +646,8 @@ def main(argv=None):
     ap.add_argument("--frames", type=int, default=0, help="cfg3 / cfg4: frame count (default 4096 / 2048)")
     ap.add_argument("--streams", type=int, default=4, help="cfg4: concurrent waves")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-segments", type=int, default=128)
+    ap.add_argument("--cpu-segments", type=int, default=0,
+                    help="AEQ segments the CPU-baseline oracle recomputes (0 = all: the whole step)")
     ap.add_argument("--ref-segments", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tensor-gradient", action="store_true",

@@ -42,7 +42,10 @@ struct AeqCfg {
     static constexpr int K = kAeqK;
     static constexpr int M = NA / 2;                         // values per lane
     static constexpr int SA = NA - K;                        // symbols per block
-    static constexpr int PRE = 8;                            // blocks per input-spectrum batch
+    // blocks per input-spectrum batch: 8 at N = 32 (one N-point transform per
+    // lane); 4 at N = 64 (one N/2-point half per lane), which halves the staging
+    // and spectrum memory so that more warps fit on an SM
+    static constexpr int PRE = NA == 64 ? 4 : 8;
     // code-size choices: at N = 32 the fully unrolled forms are small and
     // faster; at N = 64 one N/2-point code copy run twice and a partly unrolled
     // gradient keep the kernel inside the instruction cache
@@ -293,13 +296,15 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                     stage_async<C::XS>(xs2 + ((batch + 1) & 1) * C::XS, xin, t0 + C::PRE * SA - K, ch.begin, ch.end,
                                        lane);
                 {
-                    // N-point spectrum of input sq for block bq, N^-1 folded in, as
-                    // its even and odd halves in bit-reversed order: X[2k'+hh].
-                    const int bq = lane >> 2, sq = lane & 3;
-                    const uint32_t *xw = xs + bq * SA;
-                    int32_t *row = xf + (bq * 4 + sq) * C::XF_ROW;
+                    // N-point spectra of the batch's inputs, N^-1 folded in, as even
+                    // and odd halves in bit-reversed order: row (block, input) holds
+                    // X[2k'+hh] at hh HALF + bitrev_M(k')
                     if constexpr (C::FULL_INPUT) {
-                        // one N-point transform: register hh M + j holds X[2 bitrev_M(j) + hh]
+                        // lane = 4 block + input: one N-point transform, whose
+                        // register hh M + j holds X[2 bitrev_M(j) + hh]
+                        const int bq = lane >> 2, sq = lane & 3;
+                        const uint32_t *xw = xs + bq * SA;
+                        int32_t *row = xf + (bq * 4 + sq) * C::XF_ROW;
                         int32_t xv[NA];
 #pragma unroll
                         for (int j = 0; j < NA; ++j) xv[j] = sx8(xw[j], 8 * sq);
@@ -311,15 +316,15 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                                 row[hh * C::HALF + j] = rhoc(rho(rhoc(xv[hh * M + j]) * C::NINV));
                     } else {
                         // X[2k'+hh] = FNT_{N/2, alpha^2} of a_j + a_{j+N/2} (hh = 0) or
-                        // (a_j - a_{j+N/2}) alpha^j (hh = 1): one N/2-point code copy, two trips
-#pragma unroll 1
-                        for (int hh = 0; hh < 2; ++hh) {
-                            int32_t y[M];
-                            SplitInput<NA, ALPHA, 0>::run(y, xw, 8 * sq, hh != 0);
-                            fnt_fwd<M, C::ALPHA2, 17>(y);
+                        // (a_j - a_{j+N/2}) alpha^j (hh = 1); lane = 8 block + 2 input + hh
+                        static_assert(C::PRE == 4, "one half-transform per lane");
+                        const int hb = lane >> 3, hs = (lane >> 1) & 3, hh = lane & 1;
+                        int32_t y[M];
+                        SplitInput<NA, ALPHA, 0>::run(y, xs + hb * SA, 8 * hs, hh != 0);
+                        fnt_fwd<M, C::ALPHA2, 17>(y);
+                        int32_t *hrow = xf + (hb * 4 + hs) * C::XF_ROW + hh * C::HALF;
 #pragma unroll
-                            for (int j = 0; j < M; ++j) row[hh * C::HALF + j] = rhoc(rho(rhoc(y[j]) * C::NINV));
-                        }
+                        for (int j = 0; j < M; ++j) hrow[j] = rhoc(rho(rhoc(y[j]) * C::NINV));
                     }
                 }
                 __syncwarp();

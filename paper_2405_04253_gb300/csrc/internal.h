@@ -51,6 +51,7 @@ struct AeqParams {
     int32_t tensor_gradient;  // 1: gradient on the tensor cores (same results)
 };
 
-constexpr int kMaxUpdatePeriod = 64;   // keeps the summed int64 gradient exact
+constexpr int kMaxUpdatePeriod = 64;
+   // keeps the summed int64 gradient exact
 
 }  // namespace fnt

@@ -322,12 +322,12 @@ def test_chain_host_buffers_equal_device(orc):
 
 def test_chain_full_size_cfg2_sampled_segments(orc):
     """The benchmark's workload at full size (2^21 samples per polarisation,
-    segments of 1024 + 48, carried state), launched as bench.py launches it;
+    segments of 864 + 48, carried state), launched as bench.py launches it;
     sampled segments recomputed one by one by the oracle."""
     f = synth.config2()
     assert f.x.shape == (1 << 21, 2, 2)
-    plan = F.Plan(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=1024, aeq_warmup=48)
-    prm = orc.ChainParams(n_aeq=64, alpha_aeq=4080, mu_shift=9, seg_len=1024, warmup=48)
+    plan = F.Plan(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=864, aeq_warmup=48)
+    prm = orc.ChainParams(n_aeq=64, alpha_aeq=4080, mu_shift=9, seg_len=864, warmup=48)
     T0 = orc.aeq_init_taps(16, 2048)
     st = dev(T0)
     nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
@@ -359,7 +359,7 @@ def test_chain_full_size_cfg2_sampled_segments(orc):
     torch.cuda.synchronize()
     assert np.array_equal(out3.cpu().numpy(), got)
     assert torch.equal(st3, st)
-    n_seg = (nsym + 1023) // 1024
+    n_seg = (nsym + 863) // 864
     rng = np.random.default_rng(2)
     segs = sorted({0, 1, n_seg // 2, n_seg - 2, n_seg - 1, *rng.integers(0, n_seg, 15).tolist()})
     for s in segs:
