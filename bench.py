@@ -346,7 +346,9 @@ def run_fnt(args, rank, world, local_rank):
         el = reduce_max(time.perf_counter() - t0, dev)
         e2e = {"value": aggregate(n * args.e2e_steps, world, el), "unit": UNIT,
                "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(oh.numel() * 2),
-               "ms_per_step": el / args.e2e_steps * 1e3, "api": "fnt_cdc_aeq_run(host_buffers=1)"}
+               "ms_per_step": el / args.e2e_steps * 1e3, "api": "fnt_cdc_aeq_run(host_buffers=1)",
+               "transfer": "page-locked host buffers, read and written in place by the kernels over the "
+                           "host link (no staging copies); wall clock around each call"}
         st_e2e.copy_(torch.from_numpy(state_snap))
         fnt.cdc_aeq_run(plan, fr, host=True)
         e2e["bitexact_vs_device_path"] = bool(torch.equal(oh, out_check.cpu()))

@@ -182,10 +182,12 @@ typedef struct fnt_frame {
 /*
  * A batch of frames processed by one call.  `frames` is a HOST array.
  * host_buffers = 0: in/out of every frame are device pointers.
- * host_buffers = 1: in/out are host pointers (page-locked or pageable); the
- *                   library copies inputs in and outputs back through device
- *                   memory of its own, and the call returns only after the
- *                   outputs are in host memory.
+ * host_buffers = 1: in/out are host pointers.  Page-locked buffers are read
+ *                   and written in place by the kernels through their device
+ *                   mapping (on GB300, Grace memory over NVLink-C2C); pageable
+ *                   ones are copied in and back through device memory of the
+ *                   library's own.  The call returns only after the outputs
+ *                   are in host memory.
  */
 typedef struct fnt_frame_batch {
     int32_t n_frames;

@@ -226,6 +226,21 @@ namespace fnt {
 
 static bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
+// Device-accessible address of a buffer: device (or managed) memory as it is,
+// page-locked host memory through its device mapping (on GB300 the GPU reads
+// and writes Grace memory coherently over NVLink-C2C); nullptr for pageable
+// host memory.
+void *device_view(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return const_cast<void *>(p);
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
+}
+
 // Validates one frame for `op` and fills its DevFrame (pointers as given).
 static fnt_status make_frame(const fnt_plan *p, const fnt_frame &f, int op, int idx, DevFrame &df) {
     memset(&df, 0, sizeof df);
@@ -547,15 +562,29 @@ static fnt_status run(const fnt_plan *p, const fnt_frame_batch *b, int op, void 
     fnt_status st = build_work(p, b, op, w);
     if (st != FNT_OK) return st;
     layout(w);
-    // host buffers: device copies of every frame's in / out after the tables
+    // host buffers: page-locked ones are read and written in place through
+    // their device mapping; pageable ones get device copies after the tables
     std::vector<size_t> io_in, io_out;
+    std::vector<char> stage_in, stage_out;
     size_t total = w.total;
     if (b->host_buffers) {
         for (int i = 0; i < b->n_frames; ++i) {
+            const fnt_frame &f = b->frames[i];
+            DevFrame &df = w.frames[i];
+            const bool has_in = in_bytes(f, op) > 0, has_out = out_bytes(f, op, df) > 0;
+            void *vin = has_in ? device_view(f.in) : nullptr;
+            void *vout = has_out ? device_view(f.out) : nullptr;
+            stage_in.push_back(has_in && !vin);
+            stage_out.push_back(has_out && !vout);
+            if (vin) {
+                df.in = (const int8_t *)vin;
+                if (op == FNT_OP_AEQ) df.aeq_in = (int8_t *)vin;
+            }
+            if (vout) df.out = vout;
             io_in.push_back(total);
-            total += (in_bytes(b->frames[i], op) + 255) / 256 * 256;
+            if (stage_in.back()) total += (in_bytes(f, op) + 255) / 256 * 256;
             io_out.push_back(total);
-            total += (out_bytes(b->frames[i], op, w.frames[i]) + 255) / 256 * 256;
+            if (stage_out.back()) total += (out_bytes(f, op, df) + 255) / 256 * 256;
         }
     }
     char *dev = nullptr;
@@ -565,14 +594,13 @@ static fnt_status run(const fnt_plan *p, const fnt_frame_batch *b, int op, void 
         for (int i = 0; i < b->n_frames; ++i) {
             const fnt_frame &f = b->frames[i];
             DevFrame &df = w.frames[i];
+            if (stage_out[i]) df.out = dev + io_out[i];
+            if (!stage_in[i]) continue;
             df.in = (const int8_t *)(dev + io_in[i]);
-            df.out = dev + io_out[i];
             if (op == FNT_OP_AEQ) df.aeq_in = (int8_t *)df.in;
             const size_t nb = in_bytes(f, op);
-            if (nb) {
-                e = cudaMemcpyAsync(dev + io_in[i], f.in, nb, cudaMemcpyHostToDevice, stream);
-                if (e != cudaSuccess) { cudaFreeAsync(dev, stream); return cuda_fail(e, "copy input"); }
-            }
+            e = cudaMemcpyAsync(dev + io_in[i], f.in, nb, cudaMemcpyHostToDevice, stream);
+            if (e != cudaSuccess) { cudaFreeAsync(dev, stream); return cuda_fail(e, "copy input"); }
         }
     }
     st = upload_work(w, dev, stream);
@@ -580,7 +608,7 @@ static fnt_status run(const fnt_plan *p, const fnt_frame_batch *b, int op, void 
     if (st == FNT_OK && b->host_buffers) {
         for (int i = 0; i < b->n_frames; ++i) {
             const size_t nb = out_bytes(b->frames[i], op, w.frames[i]);
-            if (!nb) continue;
+            if (!nb || !stage_out[i]) continue;
             e = cudaMemcpyAsync(b->frames[i].out, dev + io_out[i], nb, cudaMemcpyDeviceToHost, stream);
             if (e != cudaSuccess) { st = cuda_fail(e, "copy output"); break; }
         }

@@ -48,6 +48,10 @@ struct Work {
 
 constexpr size_t kStateBytes = 16 * kAeqK * sizeof(int32_t);
 
+// Device-accessible address of a buffer (page-locked host memory through its
+// device mapping); nullptr for pageable host memory.
+void *device_view(const void *p);
+
 // Blocks per AEQ tap update: 0 in the descriptor means every block.
 inline int update_period(const fnt_plan_desc &d) { return d.aeq_update_period > 1 ? d.aeq_update_period : 1; }
 

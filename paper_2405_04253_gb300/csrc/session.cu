@@ -329,21 +329,6 @@ void reap(fnt_session *ss) {
     }
 }
 
-// Device-accessible address of a buffer: device (or managed) memory as it is,
-// page-locked host memory through its device mapping (on GB300 the GPU reads
-// and writes Grace memory coherently over NVLink-C2C); nullptr for pageable
-// host memory.
-void *device_view(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return const_cast<void *>(p);
-    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
-    return nullptr;
-}
-
 }  // namespace
 }  // namespace fnt
 

@@ -320,6 +320,38 @@ def test_chain_host_buffers_equal_device(orc):
     assert np.array_equal(host_out, ref)
 
 
+@pytest.mark.parametrize("pin_in,pin_out", [(True, True), (True, False), (False, True)])
+def test_host_buffers_pinned_in_place_and_pageable_staged(orc, pin_in, pin_out):
+    """host_buffers = 1: page-locked buffers are read and written in place by
+    the kernels, pageable ones are staged; every mix gives the oracle's bits,
+    for the chain, the CDC alone and the AEQ alone."""
+    rng = np.random.default_rng(40)
+
+    def host(a, pinned):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        return t.pin_memory() if pinned else t
+
+    f = synth.config2(1 << 12)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    xin = host(f.x, pin_in)
+    out = host(np.full((nsym, 4), 0x3333, np.int16), pin_out)
+    F.cdc_aeq_run(F.Plan(mu_shift=9), [F.Frame(xin, out, f.taps)], host=True)
+    ref, _ = oracle_chain(orc, f.x, f.taps, mu_shift=9)
+    assert np.array_equal(out.numpy(), ref)
+
+    x1 = rng.integers(-16, 16, (3000, 2, 2)).astype(np.int8)
+    taps = rng.integers(-32, 32, (19, 2)).astype(np.int8)
+    o1 = host(np.zeros((3000, 2, 2), np.int16), pin_out)
+    F.cdc_run(F.Plan(), [F.Frame(host(x1, pin_in), o1, taps)], host=True)
+    assert np.array_equal(o1.numpy().astype(np.int32), orc.cdc(x1, taps))
+
+    xa = rng.integers(-16, 16, (1500, 4)).astype(np.int8)
+    oa = host(np.zeros((1500, 4), np.int16), pin_out)
+    F.aeq_run(F.Plan(mu_shift=9), [F.Frame(host(xa, pin_in), oa)], host=True)
+    refa, _ = orc.aeq(xa, orc.aeq_init_taps(16, 2048), 32, 2, mu_shift=9, rde_a=64)
+    assert np.array_equal(oa.numpy(), refa)
+
+
 def test_chain_full_size_cfg2_sampled_segments(orc):
     """The benchmark's workload at full size (2^21 samples per polarisation,
     segments of 864 + 48, carried state), launched as bench.py launches it;
