@@ -223,9 +223,13 @@ typedef struct fnt_batch fnt_batch;
  * Prepares a batch once for repeated launches: validates it, builds the work
  * lists (frames split into 32-block CDC items; AEQ chains or segments sorted
  * longest first), uploads them and allocates the intermediate buffers, all in
- * device memory owned by the fnt_batch.  Device pointers only (host_buffers must
- * be 0).  use_graph = 1 records the launch into a CUDA graph on the first
- * fnt_batch_launch and replays it afterwards.
+ * device memory owned by the fnt_batch.  Buffers are device memory
+ * (host_buffers = 0) or page-locked host memory (host_buffers = 1), which the
+ * kernels read and write in place; pageable host memory is rejected with
+ * FNT_ERR_INVALID.  Launches do not wait for the device; the caller
+ * synchronises the stream before reading host outputs.  use_graph = 1 records
+ * the launch into a CUDA graph on the first fnt_batch_launch and replays it
+ * afterwards.
  */
 FNT_API fnt_status fnt_batch_create(const fnt_plan *plan, const fnt_frame_batch *batch, int32_t op,
                             int32_t use_graph, fnt_batch **out);

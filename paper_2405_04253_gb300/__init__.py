@@ -237,9 +237,10 @@ def cdc_aeq_run_noalloc(plan: Plan, frame: Frame, stream=None):
 class Batch:
     """A prepared batch (fnt_batch): work lists built and uploaded once."""
 
-    def __init__(self, plan: Plan, frames, op: int, use_graph: bool = True):
+    def __init__(self, plan: Plan, frames, op: int, use_graph: bool = True, host: bool = False):
+        """host: the frames' buffers are page-locked host memory, used in place."""
         self.plan, self.frames = plan, frames
-        b, keep = _batch(frames, False)
+        b, keep = _batch(frames, host)
         h = ctypes.c_void_p()
         check(lib().fnt_batch_create(plan.handle, ctypes.byref(b), op, 1 if use_graph else 0, ctypes.byref(h)))
         self.handle = h

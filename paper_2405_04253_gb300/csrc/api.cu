@@ -657,7 +657,6 @@ extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch 
     if (!p || !out) return fail(FNT_ERR_INVALID, "null argument");
     *out = nullptr;
     if (op < FNT_OP_CDC || op > FNT_OP_CHAIN) return fail(FNT_ERR_INVALID, "unknown op %d", op);
-    if (b && b->host_buffers) return fail(FNT_ERR_INVALID, "fnt_batch needs device buffers");
     fnt_batch *bt = new (std::nothrow) fnt_batch();
     if (!bt) return fail(FNT_ERR_NOMEM, "host memory");
     bt->plan = p;
@@ -666,6 +665,22 @@ extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch 
     if (st != FNT_OK) {
         delete bt;
         return st;
+    }
+    if (b && b->host_buffers) {
+        // page-locked host buffers are used in place through their device
+        // mapping; the prepared work cannot stage pageable ones
+        for (int i = 0; i < b->n_frames; ++i) {
+            DevFrame &df = bt->work.frames[i];
+            if (df.n == 0) continue;
+            void *vin = device_view(b->frames[i].in), *vout = device_view(b->frames[i].out);
+            if (!vin || !vout) {
+                delete bt;
+                return fail(FNT_ERR_INVALID, "fnt_batch: frame %d host buffers must be page-locked", i);
+            }
+            df.in = (const int8_t *)vin;
+            if (op == FNT_OP_AEQ) df.aeq_in = (int8_t *)vin;
+            df.out = vout;
+        }
     }
     layout(bt->work);
     const int C = (int)bt->work.item_cut.size() - 1;

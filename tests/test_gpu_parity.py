@@ -352,6 +352,31 @@ def test_host_buffers_pinned_in_place_and_pageable_staged(orc, pin_in, pin_out):
     assert np.array_equal(oa.numpy(), refa)
 
 
+def test_prepared_batch_on_page_locked_host_buffers(orc):
+    """A prepared (graph) batch over page-locked host buffers, replayed on a
+    carried state, equals the oracle step by step; pageable buffers are refused."""
+    f = synth.config2(1 << 13)
+    plan = F.Plan(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=864, aeq_warmup=48)
+    prm = orc.ChainParams(n_aeq=64, alpha_aeq=4080, mu_shift=9, seg_len=864, warmup=48)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    xh = torch.from_numpy(f.x).pin_memory()
+    oh = torch.full((nsym, 4), 0x2222, dtype=torch.int16).pin_memory()
+    T = orc.aeq_init_taps(16, 2048)
+    st = dev(T)
+    b = F.Batch(plan, [F.Frame(xh, oh, f.taps, st)], F.OP_CHAIN, use_graph=True, host=True)
+    for step in range(2):
+        b.launch()
+        torch.cuda.synchronize()
+        ref, T = orc.chain(f.x, f.taps, prm, T0=T)
+        assert np.array_equal(oh.numpy(), ref), step
+        assert np.array_equal(st.cpu().numpy(), T), step
+    b.close()
+    with pytest.raises(F.FntError) as e:
+        F.Batch(plan, [F.Frame(torch.from_numpy(f.x), torch.zeros((nsym, 4), dtype=torch.int16), f.taps)],
+                F.OP_CHAIN, host=True)
+    assert e.value.status == F.FNT_ERR_INVALID
+
+
 def test_chain_full_size_cfg2_sampled_segments(orc):
     """The benchmark's workload at full size (2^21 samples per polarisation,
     segments of 864 + 48, carried state), launched as bench.py launches it;
