@@ -76,9 +76,9 @@ def lib():
         L.orc_aeq_init_taps.restype = None
         L.orc_aeq_init_taps.argtypes = [i32, i32, vp]
         L.orc_aeq.restype = i32
-        L.orc_aeq.argtypes = [vp, ll, i32, ll, i32, i32, i32, vp, vp, i32, i32]
+        L.orc_aeq.argtypes = [vp, ll, i32, ll, i32, i32, i32, vp, vp, i32, i32, i32]
         L.orc_aeq_segmented.restype = i32
-        L.orc_aeq_segmented.argtypes = [vp, ll, i32, ll, i32, i32, i32, vp, ll, ll, vp, vp, i32, i32]
+        L.orc_aeq_segmented.argtypes = [vp, ll, i32, ll, i32, i32, i32, vp, ll, ll, vp, vp, i32, i32, i32]
         _lib = L
     return _lib
 
@@ -179,21 +179,23 @@ def aeq_init_taps(K: int = 16, w0: int = 2048) -> np.ndarray:
 
 
 def aeq(x: np.ndarray, T: np.ndarray, N: int = 32, alpha: int = 2, mu_shift: int = 20,
-        rde_a: int = 64, use_fnt: bool = True, period: int = 1):
-    """FNT-AEQ with the RDE update of eq. (6), applied every `period` blocks.
-    Returns (out int16 [n_sym, 4], T')."""
+        rde_a: int = 64, use_fnt: bool = True, period: int = 1, freq_sum: int = 0):
+    """FNT-AEQ with the RDE update of eq. (6), applied every `period` blocks;
+    freq_sum as orc_aeq.  Returns (out int16 [n_sym, 4], T')."""
     x = np.ascontiguousarray(x, dtype=np.int8)
     T = np.ascontiguousarray(T, dtype=np.int32).copy()
     K = T.shape[2]
     out = np.zeros((x.shape[0], 4), dtype=np.int16)
-    rc = lib().orc_aeq(_p(x), x.shape[0], N, alpha, K, mu_shift, rde_a, _p(T), _p(out), int(use_fnt), period)
+    rc = lib().orc_aeq(_p(x), x.shape[0], N, alpha, K, mu_shift, rde_a, _p(T), _p(out), int(use_fnt), period,
+                       freq_sum)
     if rc != 0:
         raise ValueError(f"orc_aeq failed ({rc})")
     return out, T
 
 
 def aeq_segmented(x: np.ndarray, T0: np.ndarray, N: int = 32, alpha: int = 2, mu_shift: int = 20,
-                  rde_a: int = 64, seg_len: int = 0, warmup: int = 0, use_fnt: bool = True, period: int = 1):
+                  rde_a: int = 64, seg_len: int = 0, warmup: int = 0, use_fnt: bool = True, period: int = 1,
+                  freq_sum: int = 0):
     """Segmented AEQ (each output segment re-runs from T0 with a warm-up lead)."""
     x = np.ascontiguousarray(x, dtype=np.int8)
     T0 = np.ascontiguousarray(T0, dtype=np.int32)
@@ -201,7 +203,7 @@ def aeq_segmented(x: np.ndarray, T0: np.ndarray, N: int = 32, alpha: int = 2, mu
     Tout = np.zeros_like(T0)
     out = np.zeros((x.shape[0], 4), dtype=np.int16)
     rc = lib().orc_aeq_segmented(_p(x), x.shape[0], N, alpha, K, mu_shift, rde_a, _p(T0),
-                                 seg_len, warmup, _p(Tout), _p(out), int(use_fnt), period)
+                                 seg_len, warmup, _p(Tout), _p(out), int(use_fnt), period, freq_sum)
     if rc != 0:
         raise ValueError(f"orc_aeq_segmented failed ({rc})")
     return out, Tout
@@ -223,6 +225,7 @@ class ChainParams:
     seg_len: int = 0
     warmup: int = 0
     period: int = 1
+    freq_sum: int = 0
 
 
 def chain(x: np.ndarray, taps: np.ndarray, prm: ChainParams, T0: np.ndarray | None = None,
@@ -235,8 +238,8 @@ def chain(x: np.ndarray, taps: np.ndarray, prm: ChainParams, T0: np.ndarray | No
         T0 = aeq_init_taps(prm.aeq_taps, prm.w0)
     if prm.seg_len > 0:
         return aeq_segmented(xa, T0, prm.n_aeq, prm.alpha_aeq, prm.mu_shift, prm.rde_a,
-                             prm.seg_len, prm.warmup, use_fnt, prm.period)
-    return aeq(xa, T0, prm.n_aeq, prm.alpha_aeq, prm.mu_shift, prm.rde_a, use_fnt, prm.period)
+                             prm.seg_len, prm.warmup, use_fnt, prm.period, prm.freq_sum)
+    return aeq(xa, T0, prm.n_aeq, prm.alpha_aeq, prm.mu_shift, prm.rde_a, use_fnt, prm.period, prm.freq_sum)
 
 
 def chain_segment(x: np.ndarray, taps: np.ndarray, prm: ChainParams, seg: int, T0: np.ndarray | None = None):
@@ -259,5 +262,6 @@ def chain_segment(x: np.ndarray, taps: np.ndarray, prm: ChainParams, seg: int, T
     assert xa.shape[0] == end - begin
     if T0 is None:
         T0 = aeq_init_taps(prm.aeq_taps, prm.w0)
-    out, T = aeq(xa, T0, prm.n_aeq, prm.alpha_aeq, prm.mu_shift, prm.rde_a, period=prm.period)
+    out, T = aeq(xa, T0, prm.n_aeq, prm.alpha_aeq, prm.mu_shift, prm.rde_a, period=prm.period,
+                 freq_sum=prm.freq_sum)
     return keep, out[keep - begin:], T

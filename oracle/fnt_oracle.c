@@ -330,13 +330,20 @@ void orc_aeq_init_taps(int K, int w0, int32_t *T) {
  * m >= 63 stands for mu = 0 (taps held fixed).  With an update period P > 1
  * (the paper updates every step, P = 1) G is summed over P blocks and the
  * update is applied after every P-th block and after the last block; the taps
- * stay fixed in between.  Returns 0 on success.
+ * stay fixed in between.
+ * freq_sum (FNT path only): 0 = one IFNT per (input, output, group), as in
+ * the default reading; 1 = the products of the four inputs are summed in Z_F
+ * before one IFNT per (output, group), which wraps when constraint (5) fails
+ * for the sum; 2 = as 1 for a block and polarisation only where 16 times the
+ * sum of |tap group values| over the four inputs is at most 32767 (every
+ * output decodes exactly), otherwise as 0.  Returns 0 on success.
  */
 int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, int rde_a,
-            int32_t *T, int16_t *out, int use_fnt, int period) {
+            int32_t *T, int16_t *out, int use_fnt, int period, int freq_sum) {
     const i64 F = 65537;
     const int S = N - K;
     if (n_sym < 0 || K < 1 || S < 1 || N > 256 || mu_shift < 0 || rde_a < 1 || period < 1) return 1;
+    if (freq_sum < 0 || freq_sum > 2 || (freq_sum == 1 && !use_fnt)) return 3;
     xform t;
     if (use_fnt && xform_init(&t, N, alpha, F) != 0) return 2;
     const i64 A2 = (i64)rde_a * rde_a;
@@ -346,6 +353,7 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
     i64 *wv = malloc(sizeof(i64) * N);
     i64 *Wf = malloc(sizeof(i64) * N);
     i64 *P = malloc(sizeof(i64) * N);
+    i64 *Psum = malloc(sizeof(i64) * N);
     i64 *c = malloc(sizeof(i64) * N);
     i64 *y = malloc(sizeof(i64) * S * 4);
     i64 *z = malloc(sizeof(i64) * S * 4);
@@ -374,18 +382,47 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
             }
         }
 
+        /* frequency-domain summation over the inputs (freq_sum 1, or 2 when the
+           block's guard holds for the polarisation): 16 * sum |taps of a group|
+           over the four inputs bounds the summed convolution (|x| <= 16) */
+        int sum_pol[2] = {freq_sum == 1, freq_sum == 1};
+        if (freq_sum == 2) {
+            for (int p = 0; p < 2; ++p) {
+                int ok = 1;
+                for (int s2 = 2 * p; s2 < 2 * p + 2; ++s2)
+                    for (int g = 0; g < 2; ++g) {
+                        i64 l1 = 0;
+                        for (int s1 = 0; s1 < 4; ++s1)
+                            for (int k = 0; k < K; ++k) {
+                                const int wk = W[(s2 * 4 + s1) * K + k];
+                                const i64 v = g == 0 ? floor_shift(wk, 7) : (i64)(wk & 127);
+                                l1 += v < 0 ? -v : v;
+                            }
+                        if (16 * l1 > 32767) ok = 0;
+                    }
+                sum_pol[p] = ok;
+            }
+        }
+
         memset(y, 0, sizeof(i64) * S * 4);
         for (int s2 = 0; s2 < 4; ++s2)
-            for (int s1 = 0; s1 < 4; ++s1)
-                for (int g = 0; g < 2; ++g) {
+            for (int g = 0; g < 2; ++g) {
+                const i64 weight = g == 0 ? 128 : 1;
+                const int summed = use_fnt && sum_pol[s2 / 2];
+                if (summed)
+                    for (int k = 0; k < N; ++k) Psum[k] = 0;
+                for (int s1 = 0; s1 < 4; ++s1) {
                     const int *w = W + (s2 * 4 + s1) * K;
-                    const i64 weight = g == 0 ? 128 : 1;
                     for (int m = 0; m < N; ++m) {
                         i64 v = 0;
                         if (m < K) v = g == 0 ? floor_shift(w[m], 7) : (i64)(w[m] & 127);
                         wv[m] = v;
                     }
-                    if (use_fnt) {
+                    if (summed) {
+                        for (int m = 0; m < N; ++m) wv[m] = md(wv[m], F);
+                        xfnt(&t, wv, Wf);
+                        for (int k = 0; k < N; ++k) Psum[k] = (Psum[k] + Xf[s1 * N + k] * Wf[k]) % F;
+                    } else if (use_fnt) {
                         for (int m = 0; m < N; ++m) wv[m] = md(wv[m], F);
                         xfnt(&t, wv, Wf);
                         for (int k = 0; k < N; ++k) P[k] = Xf[s1 * N + k] * Wf[k] % F;
@@ -401,6 +438,11 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
                         }
                     }
                 }
+                if (summed) {
+                    xifnt(&t, Psum, c);
+                    for (int i = 0; i < S; ++i) y[s2 * S + i] += weight * orc_decode(c[N - S + i], F);
+                }
+            }
 
         for (int i = 0; i < nvalid; ++i) {
             for (int s2 = 0; s2 < 4; ++s2) {
@@ -437,7 +479,7 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
                 }
     }
     free(Gacc);
-    free(win); free(Xf); free(wv); free(Wf); free(P); free(c); free(y); free(z); free(e); free(W);
+    free(win); free(Xf); free(wv); free(Wf); free(P); free(Psum); free(c); free(y); free(z); free(e); free(W);
     if (use_fnt) xform_free(&t);
     return 0;
 }
@@ -452,7 +494,7 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
  */
 int orc_aeq_segmented(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift,
                       int rde_a, const int32_t *T0, i64 seg_len, i64 warmup, int32_t *T_out,
-                      int16_t *out, int use_fnt, int period) {
+                      int16_t *out, int use_fnt, int period, int freq_sum) {
     int32_t *T = malloc(sizeof(int32_t) * 16 * K);
     int rc = 0;
     if (seg_len <= 0) seg_len = n_sym > 0 ? n_sym : 1;
@@ -463,7 +505,8 @@ int orc_aeq_segmented(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int m
         const i64 begin = keep - warmup > 0 ? keep - warmup : 0;
         int16_t *tmp = malloc(sizeof(int16_t) * 4 * (end - begin));
         memcpy(T, T0, sizeof(int32_t) * 16 * K);
-        rc = orc_aeq(x + begin * 4, end - begin, N, alpha, K, mu_shift, rde_a, T, tmp, use_fnt, period);
+        rc = orc_aeq(x + begin * 4, end - begin, N, alpha, K, mu_shift, rde_a, T, tmp, use_fnt, period,
+                     freq_sum);
         memcpy(out + keep * 4, tmp + (keep - begin) * 4, sizeof(int16_t) * 4 * (end - keep));
         free(tmp);
     }

@@ -371,3 +371,61 @@ def test_aeq_update_period_rules(orc):
     fixed, _ = orc.aeq(x, T0, 32, 2, mu_shift=63)
     assert np.array_equal(out1, fixed)
     assert np.array_equal(T1, (T0.astype(np.int64) + (gsum(T0, n) >> m)).astype(np.int32))
+
+
+def _centred_mod_f(v):
+    """The signed decode of a residue: v mod F in [0, F), then r - F above 32768."""
+    r = np.mod(v, 65537)
+    return np.where(r > 32768, r - 65537, r)
+
+
+def test_aeq_freq_sum_literal_is_centred_residue_of_summed_convolution(orc):
+    """freq_sum = 1 (NEXT-1, literal): per output and tap group the four inputs'
+    products are summed in Z_F before one inverse transform, so the decoded
+    group output is the centred residue mod F of the exact summed convolution,
+    sum over S1 of conv(W_g[S2][S1], x_S1) -- wrapped where it exceeds
+    constraint (5).  With fixed taps (m = 63) the whole output follows from
+    numpy integer convolutions."""
+    rng = np.random.default_rng(41)
+    n = 200
+    x = rng.integers(-16, 16, (n, 4)).astype(np.int8)
+    x[::5] = -16
+    W = rng.choice([8191, 8000, -8192, 4000, 127], size=(4, 4, 16)).astype(np.int64)
+    T0 = (W << 16).astype(np.int32)
+    for N, alpha in ((32, 2), (64, 4080)):
+        got, _ = orc.aeq(x, T0, N, alpha, mu_shift=63, freq_sum=1)
+        exact, _ = orc.aeq(x, T0, N, alpha, mu_shift=63, freq_sum=0)
+        y = np.zeros((n, 4), np.int64)
+        for s2 in range(4):
+            for g, wgt in ((0, 128), (1, 1)):
+                tot = np.zeros(n, np.int64)
+                for s1 in range(4):
+                    wg = (W[s2, s1] >> 7) if g == 0 else (W[s2, s1] & 127)
+                    tot += np.convolve(x[:, s1].astype(np.int64), wg)[:n]
+                y[:, s2] += wgt * _centred_mod_f(tot)
+        ref = np.clip(y >> 7, -32768, 32767).astype(np.int16)
+        assert np.array_equal(got, ref), N
+        assert not np.array_equal(got, exact)          # the case wraps
+
+
+def test_aeq_freq_sum_exact_where_bound_holds_and_guarded_mode_always(orc):
+    """Where 16 sum|taps| stays within 32767 the summed form decodes exactly, so
+    freq_sum = 1 equals the per-pair path; freq_sum = 2 (guarded) equals it for
+    every input, adaptation included, whether the guard holds or not."""
+    rng = np.random.default_rng(42)
+    x = rng.integers(-16, 16, (16 * 9 + 7, 4)).astype(np.int8)
+    small = np.zeros((4, 4, 16), np.int64)
+    small[[0, 1, 2, 3], [0, 1, 2, 3], 8] = 20                     # hi 0, lo 20 on the diagonal
+    small[:, :, 7] = 3
+    T_small = (small << 16).astype(np.int32)
+    for N, alpha in ((32, 2), (64, 4080)):
+        a, Ta = orc.aeq(x, T_small, N, alpha, mu_shift=63, freq_sum=0)
+        b, Tb = orc.aeq(x, T_small, N, alpha, mu_shift=63, freq_sum=1)
+        assert np.array_equal(a, b) and np.array_equal(Ta, Tb)
+        T0 = orc.aeq_init_taps(16, 2048) + rng.integers(-(1 << 22), 1 << 22, (4, 4, 16)).astype(np.int32)
+        for T in (T0, T_small, orc.aeq_init_taps(16, 2048)):
+            a, Ta = orc.aeq(x, T, N, alpha, mu_shift=8, freq_sum=0)
+            c, Tc = orc.aeq(x, T, N, alpha, mu_shift=8, freq_sum=2)
+            assert np.array_equal(a, c) and np.array_equal(Ta, Tc)
+    with pytest.raises(ValueError):
+        orc.aeq(x, T_small, 32, 2, use_fnt=False, freq_sum=1)   # no wrap to model without transforms
