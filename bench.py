@@ -222,7 +222,7 @@ class OraclePool:
 
 def _prm_kw(wl):
     return dict(n_aeq=wl["n_aeq"], alpha_aeq=wl["alpha_aeq"], mu_shift=MU_SHIFT, seg_len=wl["segment"],
-                warmup=wl["warmup"], period=wl.get("period", 1))
+                warmup=wl["warmup"], period=wl.get("period", 1), freq_sum=wl.get("freq_sum", 0))
 
 
 def _segments(x_np, taps, wl, n_seg):
@@ -250,7 +250,8 @@ def run_fnt(args, rank, world, local_rank):
     L = taps.shape[0]
     S = 64 - L + 1
     plan = fnt.Plan(n_aeq=wl["n_aeq"], alpha_aeq=wl["alpha_aeq"], mu_shift=MU_SHIFT,
-                    aeq_segment=wl["segment"], aeq_warmup=wl["warmup"], aeq_update_period=wl.get("period", 1))
+                    aeq_segment=wl["segment"], aeq_warmup=wl["warmup"], aeq_update_period=wl.get("period", 1),
+                    aeq_freq_sum=wl.get("freq_sum", 0))
     plan.set_tensor_gradient(args.tensor_gradient)
     nsym = fnt.chain_nsym(n, L)
     x = torch.from_numpy(x_np).to(dev)
@@ -402,6 +403,7 @@ def run_fnt(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload + ": " + wl["desc"], "aeq_update_period": wl.get("period", 1),
+                   "aeq_freq_sum": wl.get("freq_sum", 0),
                    "aeq_gradient": "tensor cores (exact f16 limbs, opt-in)" if args.tensor_gradient
                    else "integer pipes (int64 multiply-add)",
                    "samples_per_step": n, "symbols_per_step": nsym,
@@ -682,11 +684,14 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tensor-gradient", action="store_true",
                     help="cfg2 / cfg5: AEQ gradient on the tensor cores (bit-identical; off = integer path)")
+    ap.add_argument("--aeq-freq-sum", type=int, default=0, choices=(0, 1, 2),
+                    help="cfg2 / cfg5: AEQ inputs summed in Z_F before the inverse transform (1 literal, 2 guarded)")
     ap.add_argument("--aeq-period", type=int, default=1,
                     help="cfg2 / cfg5: AEQ blocks per tap update (1 = every block, as in eq. (6))")
     args = ap.parse_args(argv)
     for wl in WORKLOADS.values():
         wl["period"] = args.aeq_period
+        wl["freq_sum"] = args.aeq_freq_sum
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

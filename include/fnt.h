@@ -94,6 +94,15 @@ FNT_API const char *fnt_version(void);
  *                    segment counted from its warm-up start) and applied as
  *                    floor(sum / 2^m) after every P-th block and after the
  *                    run's last block; the taps are fixed in between.
+ * aeq_freq_sum       0 (default): one inverse FNT per (input, output, tap
+ *                    group), exact for every input (constraint (5) holds per
+ *                    pair).  1: the four inputs' products are summed in Z_F
+ *                    before one inverse FNT per (output, group); outputs are
+ *                    the centred residues of the summed convolutions, which
+ *                    wrap where a sum leaves [-32768, 32768].  2: summed only
+ *                    for a block and polarisation where 16 times the sum of
+ *                    |tap group values| over the inputs is at most 32767 (so
+ *                    no output wraps), per pair otherwise: results equal 0's.
  */
 typedef struct fnt_plan_desc {
     int32_t n_cdc;
@@ -108,6 +117,8 @@ typedef struct fnt_plan_desc {
     int32_t aeq_update_period;
     int64_t aeq_segment;
     int64_t aeq_warmup;
+    int32_t aeq_freq_sum;
+    int32_t reserved;
 } fnt_plan_desc;
 
 /* Fills *desc with the defaults: N=64/4080, S = N-L+1, AEQ N=32/2, K=16, m=10,

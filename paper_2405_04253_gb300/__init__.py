@@ -32,7 +32,8 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("n_cdc", ctypes.c_int32), ("alpha_cdc", ctypes.c_int32), ("cdc_step", ctypes.c_int32),
                 ("n_aeq", ctypes.c_int32), ("alpha_aeq", ctypes.c_int32), ("aeq_taps", ctypes.c_int32),
                 ("mu_shift", ctypes.c_int32), ("rde_a", ctypes.c_int32), ("tap_init", ctypes.c_int32),
-                ("aeq_update_period", ctypes.c_int32), ("aeq_segment", ctypes.c_int64), ("aeq_warmup", ctypes.c_int64)]
+                ("aeq_update_period", ctypes.c_int32), ("aeq_segment", ctypes.c_int64), ("aeq_warmup", ctypes.c_int64),
+                ("aeq_freq_sum", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class FrameC(ctypes.Structure):

@@ -232,7 +232,8 @@ __device__ __forceinline__ void gradient_mma(const uint32_t *xw, const uint32_t 
 // the P = 1 instance is the per-block update with no period bookkeeping.
 // MMA: the gradient on the tensor cores (exact, opt-in); otherwise int32 x
 // int32 -> int64 multiply-adds on the integer pipes.
-template <int NA, int64_t ALPHA, bool PER, bool MMA>
+// FS: frequency-domain summation over the inputs is compiled in (freq_sum 1 or 2).
+template <int NA, int64_t ALPHA, bool PER, bool MMA, bool FS>
 __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ frames,
                                                   const AeqChain *__restrict__ chains, int n_items,
                                                   AeqParams prm) {
@@ -279,6 +280,7 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
         const int64_t nblk = (ch.end - ch.begin + SA - 1) / SA;
         int64_t acc[4] = {0, 0, 0, 0};            // gradient of taps k0 .. k0 + 3 over the period
         int in_period = 0;                        // blocks of the current period done
+        bool fsum = FS && prm.freq_sum == 1;      // this block sums the inputs in Z_F
         // input symbols of batch 0 (PRE blocks + K history); later batches are
         // prefetched one batch ahead into the other buffer
         __syncwarp();
@@ -339,6 +341,16 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                     const int32_t W = T[k] >> 16;
                     wv[k] = g ? (W & 127) : (W >> 7);
                 }
+                if (FS && prm.freq_sum == 2) {
+                    // guard: 16 sum |w| of every (output, group) over the four
+                    // inputs within 32767, so every summed output decodes exactly
+                    int32_t l1 = 0;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) l1 += abs(wv[k]);
+                    l1 += __shfl_xor_sync(0xffffffffu, l1, 4);
+                    l1 += __shfl_xor_sync(0xffffffffu, l1, 8);
+                    fsum = __all_sync(0xffffffffu, 16 * l1 <= 32767);
+                }
                 SplitTaps<NA, ALPHA, 0>::run(y, wv, odd);
 #pragma unroll
                 for (int j = K; j < M; ++j) y[j] = 0;
@@ -357,12 +369,28 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
             const int32_t *xrow = xf + (bb * 4 + s1) * C::XF_ROW + h * C::HALF;
 #pragma unroll
             for (int j = 0; j < M; ++j) y[j] = rho(rhoc(y[j]) * xrow[j]);
+            if (FS && fsum) {
+                // frequency-domain summation: the four input lanes of an (output,
+                // group, half) all hold the sum of their products in Z_F
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    y[j] = rho(y[j] + __shfl_xor_sync(0xffffffffu, y[j], 4));
+                    y[j] = rho(y[j] + __shfl_xor_sync(0xffffffffu, y[j], 8));
+                }
+            }
             fnt_inv<M, C::ALPHA2, 17>(y);
             int32_t c[M];
             JoinHalves<NA, C::AINV, 0, 0>::run(y, c, odd);
+            if (FS && fsum) {
+                // a summed output may exceed the per-pair bound (and wraps with
+                // freq_sum = 1): the exact signed decode of the residue
+#pragma unroll
+                for (int j = 0; j < M; ++j) c[j] = decode(c[j]);
+            }
             {
-                // outputs n = h*M + j for n in [K, NA) -> block position i = n - K
-                const int32_t wgt = g ? 1 : 128;
+                // outputs n = h*M + j for n in [K, NA) -> block position i = n - K;
+                // with summation only the first input lane contributes
+                const int32_t wgt = FS && fsum && s1 != 0 ? 0 : (g ? 1 : 128);
                 int32_t *rrow = red + task * C::RED_ROW;
 #pragma unroll
                 for (int j = 0; j < M; ++j) {
@@ -492,18 +520,24 @@ size_t aeq_smem_bytes(int na, int warps, int period) {
     return (size_t)warps * words * sizeof(uint32_t);
 }
 
-template <int NA, int64_t ALPHA, bool PER, bool MMA>
+template <int NA, int64_t ALPHA, bool PER, bool MMA, bool FS>
 static cudaError_t aeq_configure_one() {
-    return cudaFuncSetAttribute(aeq_kernel<NA, ALPHA, PER, MMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(aeq_kernel<NA, ALPHA, PER, MMA, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)aeq_smem_bytes(NA, 4, PER ? 2 : 1));
+}
+
+template <int NA, int64_t ALPHA, bool PER, bool MMA>
+static cudaError_t aeq_configure_fs() {
+    cudaError_t e = aeq_configure_one<NA, ALPHA, PER, MMA, false>();
+    return e == cudaSuccess ? aeq_configure_one<NA, ALPHA, PER, MMA, true>() : e;
 }
 
 template <int NA, int64_t ALPHA>
 static cudaError_t aeq_configure_n() {
-    cudaError_t e = aeq_configure_one<NA, ALPHA, false, false>();
-    if (e == cudaSuccess) e = aeq_configure_one<NA, ALPHA, true, false>();
-    if (e == cudaSuccess) e = aeq_configure_one<NA, ALPHA, false, true>();
-    if (e == cudaSuccess) e = aeq_configure_one<NA, ALPHA, true, true>();
+    cudaError_t e = aeq_configure_fs<NA, ALPHA, false, false>();
+    if (e == cudaSuccess) e = aeq_configure_fs<NA, ALPHA, true, false>();
+    if (e == cudaSuccess) e = aeq_configure_fs<NA, ALPHA, false, true>();
+    if (e == cudaSuccess) e = aeq_configure_fs<NA, ALPHA, true, true>();
     return e;
 }
 
@@ -512,24 +546,32 @@ cudaError_t aeq_configure() {
     return e == cudaSuccess ? aeq_configure_n<32, 2>() : e;
 }
 
+template <int NA, int64_t ALPHA, bool PER, bool MMA>
+static void aeq_launch_fs(dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const DevFrame *frames,
+                          const AeqChain *chains, int n_items, AeqParams prm) {
+    if (prm.freq_sum != 0)
+        aeq_kernel<NA, ALPHA, PER, MMA, true><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+    else
+        aeq_kernel<NA, ALPHA, PER, MMA, false><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+}
+
 template <int NA, int64_t ALPHA>
 static void aeq_launch_n(dim3 grid, dim3 block, size_t smem, cudaStream_t stream, const DevFrame *frames,
                          const AeqChain *chains, int n_items, AeqParams prm, bool mma) {
     const bool per = prm.period > 1;
     if (mma) {
         if (per)
-            aeq_kernel<NA, ALPHA, true, true><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+            aeq_launch_fs<NA, ALPHA, true, true>(grid, block, smem, stream, frames, chains, n_items, prm);
         else
-            aeq_kernel<NA, ALPHA, false, true><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+            aeq_launch_fs<NA, ALPHA, false, true>(grid, block, smem, stream, frames, chains, n_items, prm);
     } else {
         if (per)
-            aeq_kernel<NA, ALPHA, true, false><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+            aeq_launch_fs<NA, ALPHA, true, false>(grid, block, smem, stream, frames, chains, n_items, prm);
         else
-            aeq_kernel<NA, ALPHA, false, false><<<grid, block, smem, stream>>>(frames, chains, n_items, prm);
+            aeq_launch_fs<NA, ALPHA, false, false>(grid, block, smem, stream, frames, chains, n_items, prm);
     }
 }
 
-// Work items are (chain, polarisation) pairs: 2 per chain.
 cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,
                        int warps, int grid, cudaStream_t stream) {
     if (n_chains <= 0) return cudaSuccess;

@@ -105,6 +105,7 @@ extern "C" void fnt_plan_desc_default(fnt_plan_desc *d) {
     d->aeq_segment = 0;
     d->aeq_warmup = 0;
     d->aeq_update_period = 0;
+    d->aeq_freq_sum = 0;
 }
 
 static bool g_configured = false;
@@ -139,6 +140,7 @@ extern "C" fnt_status fnt_plan_create(const fnt_plan_desc *d, fnt_plan **out) {
     if (d->aeq_segment < 0 || d->aeq_warmup < 0) return fail(FNT_ERR_INVALID, "negative AEQ segment/warmup");
     if (d->aeq_update_period < 0 || d->aeq_update_period > kMaxUpdatePeriod)
         return fail(FNT_ERR_INVALID, "aeq_update_period must be in [0, %d]", kMaxUpdatePeriod);
+    if (d->aeq_freq_sum < 0 || d->aeq_freq_sum > 2) return fail(FNT_ERR_INVALID, "aeq_freq_sum must be 0, 1 or 2");
     fnt_status st = configure_kernels();
     if (st != FNT_OK) return st;
 
@@ -493,7 +495,7 @@ static fnt_status launch_aeq_range(const fnt_plan *p, const Work &w, const char 
                                    cudaStream_t stream) {
     if (c1 <= c0) return FNT_OK;
     const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
-    AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d), p->tensor_gradient};
+    AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d), p->tensor_gradient, p->d.aeq_freq_sum};
     cudaError_t e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(dev + w.off_chains) + c0, c1 - c0, prm,
                                p->aeq_warps, 0, stream);
     return e == cudaSuccess ? FNT_OK : cuda_fail(e, "aeq kernel launch");

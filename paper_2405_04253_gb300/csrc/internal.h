@@ -49,6 +49,7 @@ struct AeqParams {
     int32_t rde_a;
     int32_t period;       // blocks per tap update, >= 1
     int32_t tensor_gradient;  // 1: gradient on the tensor cores (same results)
+    int32_t freq_sum;     // 0 per pair, 1 inputs summed in Z_F, 2 summed where the bound guard holds
 };
 
 constexpr int kMaxUpdatePeriod = 64;

@@ -191,6 +191,54 @@ def test_aeq_segmented_matches_oracle(orc, na, alpha):
     assert np.array_equal(got2, ref2)
 
 
+@pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("taps", ["init", "random", "wrapping", "small"])
+def test_aeq_freq_sum_matches_oracle(orc, na, alpha, mode, taps):
+    """Frequency-domain summation over the inputs (literal: wraps like the
+    oracle's; guarded: equal to the per-pair path), adaptive, with an update
+    period and with the tensor-core gradient too."""
+    rng = np.random.default_rng(na + 10 * mode + len(taps))
+    x = rng.integers(-16, 16, (1500, 4)).astype(np.int8)
+    if taps == "init":
+        T0 = orc.aeq_init_taps(16, 2048)
+    elif taps == "random":
+        T0 = orc.aeq_init_taps(16, 2048) + rng.integers(-(1 << 22), 1 << 22, (4, 4, 16)).astype(np.int32)
+    elif taps == "wrapping":
+        x[::4] = -16
+        T0 = (rng.choice([8191, 8000, -8192, 4000, 127], size=(4, 4, 16)).astype(np.int64) << 16).astype(np.int32)
+    else:
+        W = np.zeros((4, 4, 16), np.int64)
+        W[[0, 1, 2, 3], [0, 1, 2, 3], 8] = 20
+        W[:, :, 7] = 3
+        T0 = (W << 16).astype(np.int32)
+    for mu, period, tensor in ((10, 1, False), (12, 3, True), (63, 1, False)):
+        plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=mu, aeq_update_period=period, aeq_freq_sum=mode)
+        plan.set_tensor_gradient(tensor)
+        got, Tg = run_aeq(plan, x, T0)
+        ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=mu, rde_a=64, period=period, freq_sum=mode)
+        assert np.array_equal(got, ref), (mu, period, tensor)
+        assert np.array_equal(Tg, Tr), (mu, period, tensor)
+        if mode == 2:
+            base, _ = orc.aeq(x, T0, na, alpha, mu_shift=mu, rde_a=64, period=period)
+            assert np.array_equal(got, base)
+
+
+def test_chain_freq_sum_guarded_segmented(orc):
+    f = synth.config2(1 << 14)
+    kw = dict(n_aeq=64, alpha_aeq=4080, mu_shift=9)
+    plan = F.Plan(aeq_segment=864, aeq_warmup=48, aeq_freq_sum=2, **kw)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    out = i16((nsym, 4))
+    T0 = orc.aeq_init_taps(16, 2048)
+    st = dev(T0)
+    F.cdc_aeq_run(plan, [F.Frame(dev(f.x), out, f.taps, st)])
+    torch.cuda.synchronize()
+    ref, Tr = orc.chain(f.x, f.taps, orc.ChainParams(seg_len=864, warmup=48, **kw), T0=T0)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    assert np.array_equal(st.cpu().numpy(), Tr)
+
+
 @pytest.mark.parametrize("tensor", [False, True])
 @pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
 @pytest.mark.parametrize("period,n", [(2, 1000), (3, 333), (5, 4099), (64, 5000), (64, 700), (4, 16)])

@@ -74,6 +74,10 @@ def test_plan_rejects_invalid_radix_without_gpu():
             fnt.Plan(aeq_update_period=bad)
         assert e.value.status == fnt.FNT_ERR_INVALID
     assert fnt.default_desc().aeq_update_period == 0
+    with pytest.raises(fnt.FntError) as e:
+        fnt.Plan(aeq_freq_sum=3)
+    assert e.value.status == fnt.FNT_ERR_INVALID
+    assert fnt.default_desc().aeq_freq_sum == 0
 
 
 def test_product_package_does_not_import_oracle():
