@@ -76,7 +76,7 @@ def lib():
         L.orc_aeq_init_taps.restype = None
         L.orc_aeq_init_taps.argtypes = [i32, i32, vp]
         L.orc_aeq.restype = i32
-        L.orc_aeq.argtypes = [vp, ll, i32, ll, i32, i32, i32, vp, vp, i32, i32, i32]
+        L.orc_aeq.argtypes = [vp, ll, i32, ll, i32, i32, i32, vp, vp, i32, i32, i32, i32]
         L.orc_aeq_segmented.restype = i32
         L.orc_aeq_segmented.argtypes = [vp, ll, i32, ll, i32, i32, i32, vp, ll, ll, vp, vp, i32, i32, i32]
         _lib = L
@@ -179,15 +179,18 @@ def aeq_init_taps(K: int = 16, w0: int = 2048) -> np.ndarray:
 
 
 def aeq(x: np.ndarray, T: np.ndarray, N: int = 32, alpha: int = 2, mu_shift: int = 20,
-        rde_a: int = 64, use_fnt: bool = True, period: int = 1, freq_sum: int = 0):
+        rde_a: int = 64, use_fnt: bool = True, period: int = 1, freq_sum: int = 0, hist: int = 0):
     """FNT-AEQ with the RDE update of eq. (6), applied every `period` blocks;
-    freq_sum as orc_aeq.  Returns (out int16 [n_sym, 4], T')."""
+    freq_sum as orc_aeq.  The first `hist` rows of x are input history only
+    (read by the windows, no output).  Returns (out int16 [n_sym - hist, 4], T')."""
     x = np.ascontiguousarray(x, dtype=np.int8)
     T = np.ascontiguousarray(T, dtype=np.int32).copy()
     K = T.shape[2]
-    out = np.zeros((x.shape[0], 4), dtype=np.int16)
-    rc = lib().orc_aeq(_p(x), x.shape[0], N, alpha, K, mu_shift, rde_a, _p(T), _p(out), int(use_fnt), period,
-                       freq_sum)
+    n = x.shape[0] - hist
+    out = np.zeros((n, 4), dtype=np.int16)
+    xp = x.ctypes.data + hist * 4
+    rc = lib().orc_aeq(xp, n, N, alpha, K, mu_shift, rde_a, _p(T), _p(out), int(use_fnt), period,
+                       freq_sum, hist)
     if rc != 0:
         raise ValueError(f"orc_aeq failed ({rc})")
     return out, T
@@ -196,7 +199,8 @@ def aeq(x: np.ndarray, T: np.ndarray, N: int = 32, alpha: int = 2, mu_shift: int
 def aeq_segmented(x: np.ndarray, T0: np.ndarray, N: int = 32, alpha: int = 2, mu_shift: int = 20,
                   rde_a: int = 64, seg_len: int = 0, warmup: int = 0, use_fnt: bool = True, period: int = 1,
                   freq_sum: int = 0):
-    """Segmented AEQ (each output segment re-runs from T0 with a warm-up lead)."""
+    """Segmented AEQ (each output segment re-runs from T0 with a warm-up lead,
+    reading the K preceding symbols of the stream as input history)."""
     x = np.ascontiguousarray(x, dtype=np.int8)
     T0 = np.ascontiguousarray(T0, dtype=np.int32)
     K = T0.shape[2]
@@ -254,6 +258,8 @@ def chain_segment(x: np.ndarray, taps: np.ndarray, prm: ChainParams, seg: int, T
     keep = seg * seg_len
     end = min(n_sym, keep + seg_len)
     begin = max(0, keep - prm.warmup) if prm.seg_len > 0 else 0
+    hist = min(begin, prm.aeq_taps)               # input history before the run
+    begin -= hist
     t_lo = 2 * begin + phase                      # first 2-sps time the segment reads
     t_hi = 2 * (end - 1) + phase + 1
     s0 = max(0, t_lo - (L - 1))                   # CDC history of the first output
@@ -263,5 +269,5 @@ def chain_segment(x: np.ndarray, taps: np.ndarray, prm: ChainParams, seg: int, T
     if T0 is None:
         T0 = aeq_init_taps(prm.aeq_taps, prm.w0)
     out, T = aeq(xa, T0, prm.n_aeq, prm.alpha_aeq, prm.mu_shift, prm.rde_a, period=prm.period,
-                 freq_sum=prm.freq_sum)
-    return keep, out[keep - begin:], T
+                 freq_sum=prm.freq_sum, hist=hist)
+    return keep, out[keep - begin - hist:], T

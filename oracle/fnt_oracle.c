@@ -336,14 +336,19 @@ void orc_aeq_init_taps(int K, int w0, int32_t *T) {
  * before one IFNT per (output, group), which wraps when constraint (5) fails
  * for the sum; 2 = as 1 for a block and polarisation only where 16 times the
  * sum of |tap group values| over the four inputs is at most 32767 (every
- * output decodes exactly), otherwise as 0.  Returns 0 on success.
+ * output decodes exactly), otherwise as 0.
+ * hist: symbols x[-hist .. -1] precede the run and are read as its input
+ * history (windows and gradient); before them the history is zero.  No output
+ * is produced for them and they take no part in the updates.  Returns 0 on
+ * success.
  */
 int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, int rde_a,
-            int32_t *T, int16_t *out, int use_fnt, int period, int freq_sum) {
+            int32_t *T, int16_t *out, int use_fnt, int period, int freq_sum, int hist) {
     const i64 F = 65537;
     const int S = N - K;
     if (n_sym < 0 || K < 1 || S < 1 || N > 256 || mu_shift < 0 || rde_a < 1 || period < 1) return 1;
     if (freq_sum < 0 || freq_sum > 2 || (freq_sum == 1 && !use_fnt)) return 3;
+    if (hist < 0) return 1;
     xform t;
     if (use_fnt && xform_init(&t, N, alpha, F) != 0) return 2;
     const i64 A2 = (i64)rde_a * rde_a;
@@ -372,7 +377,7 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
         for (int s1 = 0; s1 < 4; ++s1)
             for (int m = 0; m < N; ++m) {
                 const i64 tt = start + m;
-                win[s1 * N + m] = (tt >= 0 && tt < n_sym) ? x[tt * 4 + s1] : 0;
+                win[s1 * N + m] = (tt >= -hist && tt < n_sym) ? x[tt * 4 + s1] : 0;
             }
         if (use_fnt) {
             for (int s1 = 0; s1 < 4; ++s1) {
@@ -465,7 +470,7 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
                     i64 G = 0;
                     for (int i = 0; i < nvalid; ++i) {
                         const i64 tt = t0 + i - k;
-                        const i64 xv = tt >= 0 ? x[tt * 4 + s1] : 0;
+                        const i64 xv = tt >= -hist ? x[tt * 4 + s1] : 0;
                         G += e[(s2 / 2) * S + i] * z[s2 * S + i] * xv;
                     }
                     const int f = (s2 * 4 + s1) * K + k;
@@ -488,9 +493,11 @@ int orc_aeq(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift, i
  * Segmented AEQ for long streams (the paper is silent on streams longer than
  * its offline captures): output segment s covers times [s*L, min((s+1)*L, n));
  * its AEQ run starts `warmup` symbols earlier (at most at 0) from the taps T0,
- * sees the slice as a frame of its own, and only the segment's own times are
- * kept.  seg_len <= 0 means one unsegmented run.  T_out (may be NULL) receives
- * the last segment's final taps.
+ * reads the K stream symbols before its start as input history (zero before
+ * the stream), and only the segment's own times are kept.  With fixed taps a
+ * segment therefore reproduces the unsegmented outputs exactly.  seg_len <= 0
+ * means one unsegmented run.  T_out (may be NULL) receives the last segment's
+ * final taps.
  */
 int orc_aeq_segmented(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int mu_shift,
                       int rde_a, const int32_t *T0, i64 seg_len, i64 warmup, int32_t *T_out,
@@ -503,10 +510,11 @@ int orc_aeq_segmented(const int8_t *x, i64 n_sym, int N, i64 alpha, int K, int m
         const i64 keep = s * seg_len;
         const i64 end = keep + seg_len < n_sym ? keep + seg_len : n_sym;
         const i64 begin = keep - warmup > 0 ? keep - warmup : 0;
+        const int hist = begin < K ? (int)begin : K;            /* the stream's preceding symbols */
         int16_t *tmp = malloc(sizeof(int16_t) * 4 * (end - begin));
         memcpy(T, T0, sizeof(int32_t) * 16 * K);
         rc = orc_aeq(x + begin * 4, end - begin, N, alpha, K, mu_shift, rde_a, T, tmp, use_fnt, period,
-                     freq_sum);
+                     freq_sum, hist);
         memcpy(out + keep * 4, tmp + (keep - begin) * 4, sizeof(int16_t) * 4 * (end - keep));
         free(tmp);
     }

@@ -29,7 +29,7 @@ long long orc_requant_decimate(const int32_t *z, long long n, int shift, int pha
 
 void orc_aeq_init_taps(int K, int w0, int32_t *T);
 int orc_aeq(const int8_t *x, long long n_sym, int N, long long alpha, int K, int mu_shift,
-            int rde_a, int32_t *T, int16_t *out, int use_fnt, int period, int freq_sum);
+            int rde_a, int32_t *T, int16_t *out, int use_fnt, int period, int freq_sum, int hist);
 int orc_aeq_segmented(const int8_t *x, long long n_sym, int N, long long alpha, int K,
                       int mu_shift, int rde_a, const int32_t *T0, long long seg_len,
                       long long warmup, int32_t *T_out, int16_t *out, int use_fnt, int period,

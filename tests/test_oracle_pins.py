@@ -307,9 +307,31 @@ def test_aeq_segmented_rules(orc):
     for s0 in range(0, 400, 128):
         b = max(0, s0 - 40)
         e = min(400, s0 + 128)
-        ref, Tr = orc.aeq(x[b:e], T0, 32, 2, mu_shift=8)
+        h = min(b, 16)                       # the K stream symbols before the run are its history
+        ref, Tr = orc.aeq(x[b - h:e], T0, 32, 2, mu_shift=8, hist=h)
         assert np.array_equal(seg[s0:e], ref[s0 - b:])
     assert np.array_equal(Ts, Tr)
+
+
+def test_aeq_segments_continue_the_stream_with_fixed_taps(orc):
+    """With fixed taps (mu = 0) every output depends on the 16 inputs up to it
+    alone, so segments that read the stream's preceding symbols as history
+    reproduce the unsegmented run exactly, with or without warm-up, ragged
+    last segment included -- and equal the plain 4x4 MIMO convolution."""
+    rng = np.random.default_rng(19)
+    x = rng.integers(-16, 16, (1000, 4)).astype(np.int8)
+    W = rng.integers(-8192, 8192, (4, 4, 16)).astype(np.int64)
+    T0 = (W << 16).astype(np.int32)
+    for N, alpha in ((32, 2), (64, 4080)):
+        plain, _ = orc.aeq(x, T0, N, alpha, mu_shift=63)
+        for seg_len, warm in ((100, 0), (48, 0), (333, 20), (7, 0)):
+            got, _ = orc.aeq_segmented(x, T0, N, alpha, mu_shift=63, seg_len=seg_len, warmup=warm)
+            assert np.array_equal(got, plain), (N, seg_len, warm)
+    y = np.zeros((1000, 4), np.int64)
+    for s2 in range(4):
+        for s1 in range(4):
+            y[:, s2] += np.convolve(x[:, s1].astype(np.int64), W[s2, s1])[:1000]
+    assert np.array_equal(plain, np.clip(y >> 7, -32768, 32767))
 
 
 def test_aeq_converges_on_synthetic_16qam(orc):
