@@ -6,8 +6,8 @@ requantise + resample, FNT-AEQ with RDE adaptation) over one batch of synthetic
 input already resident in device memory.  Default workload: one PDM-16QAM
 stream, 40 GBaud at 2 samples/symbol, 2^20 symbols per polarisation, 75 km
 (17 CD taps, 6 bit), 5-bit I/Q, AEQ 4x4 RV-MIMO at N = 64 / radix 4080 in
-segments of 864 symbols (18 AEQ blocks) with 48 warm-up symbols (one block,
-so the first kept output has its full 16-tap history), every segment starting from
+segments of 864 symbols (18 AEQ blocks) that read the 16 preceding symbols of
+the stream as input history, every segment starting from
 the tap state the previous step ended with (a stream processed step by step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fnt|reference]
@@ -42,11 +42,11 @@ UNIT = "Gsamples/s"
 # ---------------------------------------------------------------- workload ----
 
 WORKLOADS = {
-    "cfg2": dict(n_sym=1 << 20, km=75.0, n_aeq=64, alpha_aeq=4080, segment=864, warmup=48,
+    "cfg2": dict(n_sym=1 << 20, km=75.0, n_aeq=64, alpha_aeq=4080, segment=864, warmup=0,
                  desc="PDM-16QAM 40 GBaud 2 sps, 2^20 symbols/pol (2^21 samples), 75 km, 17 CD taps (6 bit), "
                       "5-bit I/Q, FNT-CDC N=64 alpha=4080 S=48 + FNT-AEQ 4x4 RV-MIMO N=64 alpha=4080 K=16, "
-                      "AEQ segments of 864 symbols (18 blocks) + 48 warm-up (one block) starting from the stream's "
-                      "carried taps"),
+                      "AEQ segments of 864 symbols (18 blocks) starting from the stream's carried taps, each "
+                      "reading the 16 preceding symbols of the stream as input history"),
     "cfg5": dict(n_sym=1 << 26, km=80.0, n_aeq=32, alpha_aeq=2, segment=1 << 16, warmup=1 << 12,
                  desc="PDM bandwidth stress, one stream of 2^27 samples/pol (a generated 2^23-sample stretch "
                       "repeated), 80 km, 19 CD taps, FNT-AEQ N=32 alpha=2, segments 2^16 + 2^12 warm-up from "

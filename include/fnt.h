@@ -84,10 +84,13 @@ FNT_API const char *fnt_version(void);
  *                    per frame.  With segments, output segment s covers symbols
  *                    [s*seg, (s+1)*seg) and its AEQ run starts aeq_warmup symbols
  *                    earlier (not before 0) from the frame's initial taps (its
- *                    state, or the plan's taps) with zero history, as if that
- *                    slice were a frame of its own; only the segment's own
- *                    outputs are kept.  Segments run in parallel.
- * aeq_warmup         warm-up symbols of each segment (ignored without segments).
+ *                    state, or the plan's taps), reading the K = 16 symbols of
+ *                    the frame before its start as input history (zero before
+ *                    the frame); only the segment's own outputs are kept.  With
+ *                    fixed taps the segments reproduce the serial outputs
+ *                    exactly.  Segments run in parallel.
+ * aeq_warmup         symbols of adaptation each segment runs before its own
+ *                    outputs (ignored without segments; 0 is allowed).
  * aeq_update_period  P, AEQ blocks per tap update, 0..64 (0 and 1: every block,
  *                    the paper's eq. (6) schedule).  For P > 1 the gradient G of
  *                    eq. (6) is summed over P blocks of a run (a frame, or a

@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
         // input symbols of batch 0 (PRE blocks + K history); later batches are
         // prefetched one batch ahead into the other buffer
         __syncwarp();
-        stage_async<C::XS>(xs2, xin, ch.begin - K, ch.begin, ch.end, lane);
+        stage_async<C::XS>(xs2, xin, ch.begin - K, ch.lo, ch.end, lane);
         const uint32_t *xs = xs2;
         for (int64_t blk = 0; blk < nblk; ++blk) {
             const int bb = (int)(blk % C::PRE);
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                 cp_async_wait_all();
                 __syncwarp();
                 if (blk + C::PRE < nblk)
-                    stage_async<C::XS>(xs2 + ((batch + 1) & 1) * C::XS, xin, t0 + C::PRE * SA - K, ch.begin, ch.end,
+                    stage_async<C::XS>(xs2 + ((batch + 1) & 1) * C::XS, xin, t0 + C::PRE * SA - K, ch.lo, ch.end,
                                        lane);
                 {
                     // N-point spectra of the batch's inputs, N^-1 folded in, as even

@@ -353,6 +353,7 @@ static void add_aeq_chains(const fnt_plan *p, const DevFrame &df, int fi, const 
         c.keep = k;
         c.end = std::min(n, k + seg);
         c.begin = std::max<int64_t>(0, k - p->d.aeq_warmup);
+        c.lo = std::max<int64_t>(0, c.begin - kAeqK);   // the stream's preceding symbols
         c.write_state = (df.state != nullptr) && c.end == n;
         c.init = init_dev;
         c.init_copy = copy;

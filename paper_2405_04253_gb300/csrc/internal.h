@@ -35,14 +35,15 @@ static_assert(sizeof(DevFrame) == 128 + 0 || sizeof(DevFrame) % 16 == 0, "DevFra
 struct alignas(16) AeqChain {
     int32_t frame;
     int32_t write_state;   // 1: write the final taps to the frame's state
-    int64_t begin;         // first symbol the run processes (history is zero before it)
+    int64_t begin;         // first symbol the run processes
+    int64_t lo;            // first symbol its windows may read as input history (zero before it)
     int64_t keep;          // first symbol whose output is stored
     int64_t end;           // one past the last symbol
     const int32_t *init;   // initial taps (frame state, a copy of it, or the plan's initial taps)
     int32_t init_copy;     // host side only: index of the state copy `init` must point to, or -1
     int32_t need_item;     // host side only: last CDC work item whose output this chain reads
 };
-static_assert(sizeof(AeqChain) == 48, "AeqChain layout");
+static_assert(sizeof(AeqChain) == 64, "AeqChain layout");
 
 struct AeqParams {
     int32_t mu_shift;
@@ -52,7 +53,6 @@ struct AeqParams {
     int32_t freq_sum;     // 0 per pair, 1 inputs summed in Z_F, 2 summed where the bound guard holds
 };
 
-constexpr int kMaxUpdatePeriod = 64;
-   // keeps the summed int64 gradient exact
+constexpr int kMaxUpdatePeriod = 64;   // keeps the summed int64 gradient exact
 
 }  // namespace fnt

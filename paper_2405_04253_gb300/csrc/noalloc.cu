@@ -143,6 +143,7 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
             c.keep = k;
             c.end = std::min(nsym, k + seg);
             c.begin = std::max<int64_t>(0, k - p->d.aeq_warmup);
+            c.lo = std::max<int64_t>(0, c.begin - kAeqK);   // the stream's preceding symbols
             c.write_state = (f->aeq_state != nullptr) && c.end == nsym;
             // segments start from the state as it was at the call (copied below)
             c.init = f->aeq_state ? (const int32_t *)(base + kOffInit) : p->d_init;

@@ -231,6 +231,7 @@ fnt_status launch_wave(fnt_session *ss, Slot &slot) {
                 c.keep = k;
                 c.end = std::min(r.n_sym, k + seg);
                 c.begin = std::max<int64_t>(0, k - ss->plan->d.aeq_warmup);
+                c.lo = std::max<int64_t>(0, c.begin - kAeqK);   // the stream's preceding symbols
                 c.write_state = c.end == r.n_sym;
                 c.init = (const int32_t *)(ss->arena_mem + r.off_init);
                 c.init_copy = -1;

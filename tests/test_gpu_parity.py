@@ -427,12 +427,12 @@ def test_prepared_batch_on_page_locked_host_buffers(orc):
 
 def test_chain_full_size_cfg2_sampled_segments(orc):
     """The benchmark's workload at full size (2^21 samples per polarisation,
-    segments of 864 + 48, carried state), launched as bench.py launches it;
-    sampled segments recomputed one by one by the oracle."""
+    segments of 864 with stream history, carried state), launched as bench.py
+    launches it; sampled segments recomputed one by one by the oracle."""
     f = synth.config2()
     assert f.x.shape == (1 << 21, 2, 2)
-    plan = F.Plan(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=864, aeq_warmup=48)
-    prm = orc.ChainParams(n_aeq=64, alpha_aeq=4080, mu_shift=9, seg_len=864, warmup=48)
+    plan = F.Plan(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=864, aeq_warmup=0)
+    prm = orc.ChainParams(n_aeq=64, alpha_aeq=4080, mu_shift=9, seg_len=864, warmup=0)
     T0 = orc.aeq_init_taps(16, 2048)
     st = dev(T0)
     nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
