@@ -599,7 +599,7 @@ def run_cfg4(args):
     import paper_2405_04253_gb300 as fnt
     import synth
     tr = synth.config4(args.frames)
-    plans = {"serial": dict(), "segmented": dict(aeq_segment=1024, aeq_warmup=16)}
+    plans = {"serial": dict(), "segmented": dict(aeq_segment=1024, aeq_warmup=0)}
 
     def serve(paced: bool, plan):
         from collections import deque
