@@ -167,12 +167,32 @@ extern "C" fnt_status fnt_plan_create(const fnt_plan_desc *d, fnt_plan **out) {
         delete p;
         return cuda_fail(e, "cudaMemcpy(init taps)");
     }
+    // the per-call work memory comes from a pool of the plan's own that keeps
+    // up to kPoolKeepBytes mapped between calls (the device's default pool
+    // returns freed memory to the system at every synchronisation)
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = p->device;
+    e = cudaMemPoolCreate(&p->pool, &props);
+    if (e == cudaSuccess) {
+        uint64_t keep = kPoolKeepBytes;
+        e = cudaMemPoolSetAttribute(p->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e != cudaSuccess) {
+        if (p->pool) cudaMemPoolDestroy(p->pool);
+        cudaFree(p->d_init);
+        delete p;
+        return cuda_fail(e, "cudaMemPoolCreate");
+    }
     *out = p;
     return FNT_OK;
 }
 
 extern "C" fnt_status fnt_plan_destroy(fnt_plan *p) {
     if (!p) return FNT_OK;
+    cudaDeviceSynchronize();             // calls still in flight hold pool memory
+    cudaMemPoolDestroy(p->pool);
     cudaFree(p->d_init);
     delete p;
     return FNT_OK;
@@ -387,6 +407,16 @@ fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work 
                          [&](int a, int c) { return w.frames[a].n_sym > w.frames[c].n_sym; });
     const bool both = op != FNT_OP_AEQ && cdc_items_both(p, w);
     w.cdc_both = both;
+    {
+        size_t n_items = 0, n_chains = 0;
+        for (const DevFrame &df : w.frames) {
+            if (op != FNT_OP_AEQ) n_items += (size_t)(((df.n + df.S - 1) / df.S + kBlocksPerItem - 1) / kBlocksPerItem) * 2;
+            if (op != FNT_OP_CDC)
+                n_chains += p->d.aeq_segment > 0 ? (size_t)((df.n_sym + p->d.aeq_segment - 1) / p->d.aeq_segment) : 1;
+        }
+        w.items.reserve(n_items);
+        w.chains.reserve(n_chains);
+    }
     for (int i : order) {
         const int first_item = (int)w.items.size();
         if (op != FNT_OP_AEQ) add_cdc_items(w.frames[i], i, both, w.items);
@@ -416,12 +446,14 @@ fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work 
         while (k + 1 < C && c.need_item >= w.item_cut[k + 1]) ++k;
         return k;
     };
-    // within a chunk, longest chains first
-    std::stable_sort(w.chains.begin(), w.chains.end(), [&](const AeqChain &a, const AeqChain &c) {
+    // within a chunk, longest chains first (often already so: skip the sort then)
+    auto before = [&](const AeqChain &a, const AeqChain &c) {
         const int ka = chunk_of(a), kc = chunk_of(c);
         if (ka != kc) return ka < kc;
         return (a.end - a.begin) > (c.end - c.begin);
-    });
+    };
+    if (!std::is_sorted(w.chains.begin(), w.chains.end(), before))
+        std::stable_sort(w.chains.begin(), w.chains.end(), before);
     w.chain_cut.assign(C + 1, (int)w.chains.size());
     w.chain_cut[0] = 0;
     for (int k = 1; k < C; ++k) {
@@ -444,6 +476,50 @@ void layout(Work &w) {
     if (w.total == 0) w.total = 256;
 }
 
+// A page-locked host buffer per thread for table uploads, with an event that
+// marks when the last copy out of it has run (on the device it was recorded on).
+struct Staging {
+    char *buf = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    int device = -1;
+    cudaError_t reserve(size_t bytes) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (done) {
+            e = cudaEventSynchronize(done);       // the previous copy has read the buffer
+            if (e != cudaSuccess) return e;
+        }
+        if (dev != device && done) {
+            cudaEventDestroy(done);
+            done = nullptr;
+        }
+        if (!done) {
+            e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+            device = dev;
+        }
+        if (cap < bytes) {
+            if (buf) cudaFreeHost(buf);
+            buf = nullptr;
+            cap = 0;
+            e = cudaMallocHost((void **)&buf, bytes);
+            if (e != cudaSuccess) return e;
+            cap = bytes;
+        }
+        return cudaSuccess;
+    }
+};
+
+// Four per thread in rotation, so that a thread can queue a few calls ahead of
+// the device before it waits for a staging buffer.
+static Staging &thread_staging() {
+    static thread_local Staging sg[4];     // kept for the thread's life
+    static thread_local unsigned next = 0;
+    return sg[next++ & 3];
+}
+
 // Points the chain frames' intermediate buffers into the allocation and copies
 // the three tables (host -> device, on `stream`).
 fnt_status upload_work(Work &w, char *dev, cudaStream_t stream) {
@@ -452,23 +528,19 @@ fnt_status upload_work(Work &w, char *dev, cudaStream_t stream) {
             w.frames[i].aeq_in = (int8_t *)(dev + w.off_scratch + w.scratch_off[i]);
     for (AeqChain &c : w.chains)
         if (c.init_copy >= 0) c.init = (const int32_t *)(dev + w.off_init + (size_t)c.init_copy * kStateBytes);
-    cudaError_t e;
-    if (!w.frames.empty()) {
-        e = cudaMemcpyAsync(dev + w.off_frames, w.frames.data(), w.frames.size() * sizeof(DevFrame),
-                            cudaMemcpyHostToDevice, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "upload frames");
-    }
-    if (!w.items.empty()) {
-        e = cudaMemcpyAsync(dev + w.off_items, w.items.data(), w.items.size() * sizeof(int4),
-                            cudaMemcpyHostToDevice, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "upload items");
-    }
-    if (!w.chains.empty()) {
-        e = cudaMemcpyAsync(dev + w.off_chains, w.chains.data(), w.chains.size() * sizeof(AeqChain),
-                            cudaMemcpyHostToDevice, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "upload chains");
-    }
-    return FNT_OK;
+    // the three tables are contiguous in [0, off_init): one copy from a page-
+    // locked staging buffer of this thread, reused once its previous copy is done
+    const size_t bytes = w.off_init;
+    if (bytes == 0) return FNT_OK;
+    Staging &sg = thread_staging();
+    cudaError_t e = sg.reserve(bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "table staging");
+    if (!w.frames.empty()) memcpy(sg.buf + w.off_frames, w.frames.data(), w.frames.size() * sizeof(DevFrame));
+    if (!w.items.empty()) memcpy(sg.buf + w.off_items, w.items.data(), w.items.size() * sizeof(int4));
+    if (!w.chains.empty()) memcpy(sg.buf + w.off_chains, w.chains.data(), w.chains.size() * sizeof(AeqChain));
+    e = cudaMemcpyAsync(dev, sg.buf, bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(sg.done, stream);
+    return e == cudaSuccess ? FNT_OK : cuda_fail(e, "upload tables");
 }
 
 static fnt_status launch_cdc_range(const fnt_plan *p, const Work &w, const char *dev, int i0, int i1,
@@ -591,8 +663,8 @@ static fnt_status run(const fnt_plan *p, const fnt_frame_batch *b, int op, void 
         }
     }
     char *dev = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&dev, total, stream);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(FNT_ERR_NOMEM, "device memory") : cuda_fail(e, "cudaMallocAsync");
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&dev, total, p->pool, stream);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(FNT_ERR_NOMEM, "device memory") : cuda_fail(e, "cudaMallocFromPoolAsync");
     if (b->host_buffers) {
         for (int i = 0; i < b->n_frames; ++i) {
             const fnt_frame &f = b->frames[i];

@@ -20,6 +20,7 @@ struct fnt_plan {
     int chunks = 1;              // pipelined chunks of prepared chain batches (1 = off)
     int tensor_gradient = 0;     // AEQ gradient on the tensor cores (opt-in, same results)
     int cdc_pols_per_item = 0;   // CDC items: 0 auto, 1 one polarisation, 2 both
+    cudaMemPool_t pool = nullptr;  // per-call work memory, kept mapped between calls
 };
 
 namespace fnt {
@@ -47,6 +48,7 @@ struct Work {
 };
 
 constexpr size_t kStateBytes = 16 * kAeqK * sizeof(int32_t);
+constexpr uint64_t kPoolKeepBytes = 1ull << 30;   // work memory a plan keeps mapped between calls
 
 // Device-accessible address of a buffer (page-locked host memory through its
 // device mapping); nullptr for pageable host memory.
