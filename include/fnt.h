@@ -131,10 +131,14 @@ FNT_API void fnt_plan_desc_default(fnt_plan_desc *desc);
 typedef struct fnt_plan fnt_plan;
 
 /* Validates desc (eq. (4): alpha^N = 1 with order exactly N, N invertible mod F;
- * supported (N, alpha) pairs; ranges above) and creates a plan.  A plan holds no
- * per-call state and may be used from several threads and streams at once.
- * Errors: FNT_ERR_INVALID, FNT_ERR_BOUND, FNT_ERR_NOMEM. */
+ * supported (N, alpha) pairs; ranges above) and creates a plan on the current
+ * device.  A plan holds no per-call state and may be used from several threads
+ * and streams at once.  The one-shot calls take their work memory (tables and
+ * intermediate buffers) from a memory pool of the plan that keeps up to 1 GiB
+ * mapped between calls.  Errors: FNT_ERR_INVALID, FNT_ERR_BOUND,
+ * FNT_ERR_NOMEM, FNT_ERR_CUDA. */
 FNT_API fnt_status fnt_plan_create(const fnt_plan_desc *desc, fnt_plan **out);
+/* Waits for the device, then frees the plan and its memory pool. */
 FNT_API fnt_status fnt_plan_destroy(fnt_plan *plan);
 
 /* Multiplication counts of the kernels for a plan description (no device
