@@ -133,7 +133,8 @@ typedef struct fnt_plan fnt_plan;
 /* Validates desc (eq. (4): alpha^N = 1 with order exactly N, N invertible mod F;
  * supported (N, alpha) pairs; ranges above) and creates a plan on the current
  * device.  A plan holds no per-call state and may be used from several threads
- * and streams at once.  The one-shot calls take their work memory (tables and
+ * and streams at once; calls with it must be made with its device current
+ * (FNT_ERR_INVALID otherwise).  The one-shot calls take their work memory (tables and
  * intermediate buffers) from a memory pool of the plan that keeps up to 1 GiB
  * mapped between calls.  Errors: FNT_ERR_INVALID, FNT_ERR_BOUND,
  * FNT_ERR_NOMEM, FNT_ERR_CUDA. */

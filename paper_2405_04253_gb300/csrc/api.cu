@@ -6,6 +6,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -108,15 +110,29 @@ extern "C" void fnt_plan_desc_default(fnt_plan_desc *d) {
     d->aeq_freq_sum = 0;
 }
 
-static bool g_configured = false;
+// Kernel attributes (the dynamic shared memory limits) are per device: set them
+// once on every device a plan is created on.
+static std::mutex g_config_mu;
+static std::set<int> g_configured;
 
-static fnt_status configure_kernels() {
-    if (g_configured) return FNT_OK;
+static fnt_status configure_kernels(int device) {
+    std::lock_guard<std::mutex> lk(g_config_mu);
+    if (g_configured.count(device)) return FNT_OK;
     cudaError_t e = cdc_configure();
     if (e != cudaSuccess) return cuda_fail(e, "cdc_configure");
     e = aeq_configure();
     if (e != cudaSuccess) return cuda_fail(e, "aeq_configure");
-    g_configured = true;
+    g_configured.insert(device);
+    return FNT_OK;
+}
+
+// The calls of a plan run on the plan's device, which must be current.
+fnt_status fnt::check_device(const fnt_plan *p) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device) return fail(FNT_ERR_INVALID, "the plan was created on device %d, device %d is current",
+                                      p->device, dev);
     return FNT_OK;
 }
 
@@ -141,17 +157,16 @@ extern "C" fnt_status fnt_plan_create(const fnt_plan_desc *d, fnt_plan **out) {
     if (d->aeq_update_period < 0 || d->aeq_update_period > kMaxUpdatePeriod)
         return fail(FNT_ERR_INVALID, "aeq_update_period must be in [0, %d]", kMaxUpdatePeriod);
     if (d->aeq_freq_sum < 0 || d->aeq_freq_sum > 2) return fail(FNT_ERR_INVALID, "aeq_freq_sum must be 0, 1 or 2");
-    fnt_status st = configure_kernels();
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    fnt_status st = configure_kernels(device);
     if (st != FNT_OK) return st;
 
     fnt_plan *p = new (std::nothrow) fnt_plan();
     if (!p) return fail(FNT_ERR_NOMEM, "plan_create: out of host memory");
     p->d = *d;
-    cudaError_t e = cudaGetDevice(&p->device);
-    if (e != cudaSuccess) {
-        delete p;
-        return cuda_fail(e, "cudaGetDevice");
-    }
+    p->device = device;
     cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device);
     int32_t init[16 * kAeqK] = {0};
     for (int s = 0; s < 4; ++s) init[(s * 4 + s) * kAeqK + kAeqK / 2] = (int32_t)((int64_t)d->tap_init * 65536);
@@ -632,6 +647,8 @@ static size_t out_bytes(const fnt_frame &f, int op, const DevFrame &df) {
 
 static fnt_status run(const fnt_plan *p, const fnt_frame_batch *b, int op, void *stream_) {
     if (!p) return fail(FNT_ERR_INVALID, "null plan");
+    fnt_status dst = check_device(p);
+    if (dst != FNT_OK) return dst;
     cudaStream_t stream = (cudaStream_t)stream_;
     Work w;
     fnt_status st = build_work(p, b, op, w);
@@ -732,6 +749,8 @@ extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch 
     if (!p || !out) return fail(FNT_ERR_INVALID, "null argument");
     *out = nullptr;
     if (op < FNT_OP_CDC || op > FNT_OP_CHAIN) return fail(FNT_ERR_INVALID, "unknown op %d", op);
+    fnt_status dst = check_device(p);
+    if (dst != FNT_OK) return dst;
     fnt_batch *bt = new (std::nothrow) fnt_batch();
     if (!bt) return fail(FNT_ERR_NOMEM, "host memory");
     bt->plan = p;

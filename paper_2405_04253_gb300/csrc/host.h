@@ -26,6 +26,7 @@ struct fnt_plan {
 namespace fnt {
 
 fnt_status fail(fnt_status st, const char *fmt, ...);
+fnt_status check_device(const fnt_plan *p);   // FNT_ERR_INVALID unless the plan's device is current
 fnt_status cuda_fail(cudaError_t e, const char *what);
 
 int cdc_shift_of(const int8_t *taps, int L);

@@ -339,6 +339,8 @@ extern "C" fnt_status fnt_session_create(const fnt_plan *plan, int32_t n_links, 
     *out = nullptr;
     if (n_links < 1 || n_streams < 1 || n_streams > 64 || mem_cap_bytes < 4096)
         return fail(FNT_ERR_INVALID, "session: need n_links >= 1, 1 <= n_streams <= 64, mem_cap >= 4 KiB");
+    fnt_status dst = check_device(plan);
+    if (dst != FNT_OK) return dst;
     fnt_session *ss = new (std::nothrow) fnt_session();
     if (!ss) return fail(FNT_ERR_NOMEM, "host memory");
     ss->plan = plan;
