@@ -503,3 +503,43 @@ def test_pipelined_batch_equals_oracle_and_unpipelined(orc):
     for i in (0, 7, 39):
         ref, _ = orc.chain(frames_np[i][0], frames_np[i][1], orc.ChainParams(mu_shift=9))
         assert np.array_equal(outs[4][i], ref)
+
+
+def test_one_plan_from_two_threads_on_two_streams(orc):
+    """A plan is shared by threads: each thread's one-shot calls (pinned host
+    buffers, its own stream, its own staging ring, the plan's memory pool)
+    return the oracle's bits, call after call, while the other thread runs."""
+    import threading
+    rng = np.random.default_rng(50)
+    plan = F.Plan(mu_shift=9, aeq_segment=512, aeq_warmup=0)
+    prm = orc.ChainParams(mu_shift=9, seg_len=512, warmup=0)
+    cases = []
+    for t in range(2):
+        n = int(rng.integers(3000, 9000))
+        L = int(rng.choice([5, 17, 19]))
+        x = rng.integers(-16, 16, (n, 2, 2)).astype(np.int8)
+        taps = rng.integers(-32, 32, (L, 2)).astype(np.int8)
+        cases.append((x, taps, orc.chain(x, taps, prm)[0]))
+    errors = []
+
+    def worker(t):
+        try:
+            x, taps, ref = cases[t]
+            stream = torch.cuda.Stream()
+            xh = torch.from_numpy(x).pin_memory()
+            oh = torch.zeros(ref.shape, dtype=torch.int16).pin_memory()
+            for k in range(25):
+                oh.fill_(0x1111)
+                F.cdc_aeq_run(plan, [F.Frame(xh, oh, taps)], stream=stream, host=True)
+                if not np.array_equal(oh.numpy(), ref):
+                    errors.append((t, k))
+                    return
+        except Exception as e:          # reported below
+            errors.append((t, repr(e)))
+
+    th = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for t_ in th:
+        t_.start()
+    for t_ in th:
+        t_.join()
+    assert errors == []
