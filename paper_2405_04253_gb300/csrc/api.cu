@@ -486,7 +486,8 @@ void layout(Work &w) {
     w.off_items = up(w.off_frames + w.frames.size() * sizeof(DevFrame));
     w.off_chains = up(w.off_items + w.items.size() * sizeof(int4));
     w.off_init = up(w.off_chains + w.chains.size() * sizeof(AeqChain));
-    w.off_scratch = up(w.off_init + w.init_src.size() * kStateBytes);
+    w.off_spec = up(w.off_init + w.init_src.size() * kStateBytes);
+    w.off_scratch = up(w.off_spec + (w.op != FNT_OP_AEQ ? w.frames.size() * kSpecBytes : 0));
     w.total = up(w.off_scratch + (size_t)w.scratch_bytes);
     if (w.total == 0) w.total = 256;
 }
@@ -535,9 +536,16 @@ static Staging &thread_staging() {
     return sg[next++ & 3];
 }
 
-// Points the chain frames' intermediate buffers into the allocation and copies
-// the three tables (host -> device, on `stream`).
+void point_spectra(Work &w, char *dev) {
+    if (w.op == FNT_OP_AEQ) return;
+    for (size_t i = 0; i < w.frames.size(); ++i)
+        w.frames[i].hspec = (int32_t *)(dev + w.off_spec + i * kSpecBytes);
+}
+
+// Points the chain frames' intermediate buffers and tap-spectrum slots into the
+// allocation and copies the three tables (host -> device, on `stream`).
 fnt_status upload_work(Work &w, char *dev, cudaStream_t stream) {
+    point_spectra(w, dev);
     if (w.op == FNT_OP_CHAIN)
         for (size_t i = 0; i < w.frames.size(); ++i)
             w.frames[i].aeq_in = (int8_t *)(dev + w.off_scratch + w.scratch_off[i]);
@@ -589,9 +597,18 @@ static fnt_status launch_aeq_range(const fnt_plan *p, const Work &w, const char 
     return e == cudaSuccess ? FNT_OK : cuda_fail(e, "aeq kernel launch");
 }
 
+static fnt_status launch_spectra(const Work &w, const char *dev, cudaStream_t stream) {
+    if (w.op == FNT_OP_AEQ || w.spectra_ready || w.frames.empty()) return FNT_OK;
+    cudaError_t e = cdc_spectra_launch((const DevFrame *)(dev + w.off_frames), (int)w.frames.size(), stream);
+    return e == cudaSuccess ? FNT_OK : cuda_fail(e, "tap spectra launch");
+}
+
 fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream, int stages) {
     fnt_status st = FNT_OK;
-    if ((stages & 1) && w.op != FNT_OP_AEQ) st = launch_cdc_range(p, w, dev, 0, (int)w.items.size(), stream);
+    if ((stages & 1) && w.op != FNT_OP_AEQ) {
+        st = launch_spectra(w, dev, stream);
+        if (st == FNT_OK) st = launch_cdc_range(p, w, dev, 0, (int)w.items.size(), stream);
+    }
     if (st == FNT_OK && (stages & 2) && w.op != FNT_OP_CDC && !w.chains.empty()) {
         st = copy_initial_taps(w, dev, stream);
         if (st == FNT_OK) st = launch_aeq_range(p, w, dev, 0, (int)w.chains.size(), stream);
@@ -603,6 +620,7 @@ fnt_status launch_pipelined(const fnt_plan *p, const Work &w, const char *dev, c
                             const std::vector<cudaStream_t> &side, const std::vector<cudaEvent_t> &ev) {
     const int C = (int)w.item_cut.size() - 1;
     fnt_status st = copy_initial_taps(w, dev, stream);
+    if (st == FNT_OK) st = launch_spectra(w, dev, stream);
     for (int k = 0; k < C && st == FNT_OK; ++k) {
         st = launch_cdc_range(p, w, dev, w.item_cut[k], w.item_cut[k + 1], stream);
         if (st != FNT_OK) break;
@@ -625,6 +643,7 @@ fnt_status launch_pipelined(const fnt_plan *p, const Work &w, const char *dev, c
 int work_kernel_count(const Work &w) {
     const int C = (int)w.item_cut.size() - 1;
     int k = 0;
+    if (w.op != FNT_OP_AEQ && !w.spectra_ready && !w.frames.empty()) k += 1;   // tap spectra
     if (w.op != FNT_OP_AEQ) k += C > 1 ? C : (w.items.empty() ? 0 : 1);
     if (w.op != FNT_OP_CDC) {
         if (C > 1) {
@@ -790,7 +809,11 @@ extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch 
         return e == cudaErrorMemoryAllocation ? fail(FNT_ERR_NOMEM, "device memory") : cuda_fail(e, "cudaMalloc");
     }
     st = upload_work(bt->work, bt->dev, 0);
+    // the taps of a prepared batch never change: its tap spectra are computed
+    // once here, and its launches (and graph) hold only the CDC and AEQ kernels
+    if (st == FNT_OK) st = launch_spectra(bt->work, bt->dev, 0);
     if (st == FNT_OK) {
+        bt->work.spectra_ready = true;
         e = cudaStreamSynchronize(0);
         if (e != cudaSuccess) st = cuda_fail(e, "upload sync");
     }

@@ -90,6 +90,28 @@ __device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, cons
     }
 }
 
+// Tap spectra of each frame, once per frame: H_u[k] and H_v[k] (u = h_re +
+// 2^8 h_im, v = h_re - 2^8 h_im) times N^-1 2^-1, entry i holding
+// k = bitrev(i), as centred residues: thread t < 64 computes H_u at i = t,
+// thread 64 + i computes H_v.  One CTA of 128 threads per frame.
+__global__ void __launch_bounds__(2 * kN) cdc_spectra_kernel(const DevFrame *__restrict__ frames, int n_frames) {
+    __shared__ int32_t s_pow[kN];
+    if (threadIdx.x < kN) s_pow[threadIdx.x] = zcent(zpow(kAlpha, threadIdx.x));
+    __syncthreads();
+    const int i = threadIdx.x & (kN - 1);
+    const int32_t sg = threadIdx.x < kN ? 256 : -256;
+    const int k = (int)(__brev((unsigned)i) >> 26);
+    for (int f = blockIdx.x; f < n_frames; f += gridDim.x) {
+        const DevFrame &fr = frames[f];
+        int32_t a = 0;
+        for (int m = 0; m < fr.L; ++m) {
+            const int32_t hr = fr.taps[2 * m], hi = fr.taps[2 * m + 1];
+            a += rho((hr + sg * hi) * s_pow[(m * k) & (kN - 1)]);     // |a| < 31 * 98304 < 2^22
+        }
+        fr.hspec[threadIdx.x] = rhoc(rho(rhoc(a) * kHScale));
+    }
+}
+
 // BOTH: items may cover both polarisations of a PDM frame (item.w = 2); such a
 // warp runs the two blocks of each lane back to back from one window fill and
 // one tap-spectrum set, and stores each symbol's 4-byte word at once.  That
@@ -98,10 +120,6 @@ template <bool CHAIN, bool BOTH>
 __global__ void __launch_bounds__(128, BOTH ? 2 : 3) cdc_kernel(const DevFrame *__restrict__ frames,
                                                      const int4 *__restrict__ items, int n_items) {
     extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ int32_t s_pow[kN];
-    if (threadIdx.x < kN) s_pow[threadIdx.x] = zcent(zpow(kAlpha, threadIdx.x));
-    __syncthreads();
-
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
@@ -120,21 +138,9 @@ __global__ void __launch_bounds__(128, BOTH ? 2 : 3) cdc_kernel(const DevFrame *
         const int npol = fr.n_pol;
         const int64_t n = fr.n;
 
-        // Tap spectra H[k] = sum_n h[n] alpha^(nk), k = bitrev(i), lanes i and i + 32.
+        // the frame's tap spectra (cdc_spectra_kernel), 4 words per lane
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int i = lane + 32 * h;
-            const int k = (int)(__brev((unsigned)i) >> 26);
-            int32_t au = 0, av = 0;
-            for (int m = 0; m < L; ++m) {
-                const int32_t hr = fr.taps[2 * m], hi = fr.taps[2 * m + 1];
-                const int32_t pw = s_pow[(m * k) & (kN - 1)];
-                au += rho((hr + 256 * hi) * pw);
-                av += rho((hr - 256 * hi) * pw);
-            }
-            hs[i] = rhoc(rho(rhoc(au) * kHScale));
-            hs[kN + i] = rhoc(rho(rhoc(av) * kHScale));
-        }
+        for (int h = 0; h < 4; ++h) hs[lane + 32 * h] = fr.hspec[lane + 32 * h];
 
         // Input windows: window l covers samples base + l*S + [0, 64).  All 64
         // loads of a lane are in flight at once: asynchronous 4-byte copies
@@ -249,6 +255,12 @@ cudaError_t cdc_configure() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(cdc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     return e;
+}
+
+cudaError_t cdc_spectra_launch(const DevFrame *frames, int n_frames, cudaStream_t stream) {
+    if (n_frames <= 0) return cudaSuccess;
+    cdc_spectra_kernel<<<n_frames < 65535 ? n_frames : 65535, 2 * kN, 0, stream>>>(frames, n_frames);
+    return cudaGetLastError();
 }
 
 cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, bool both, int warps,

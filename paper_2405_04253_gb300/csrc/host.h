@@ -37,6 +37,7 @@ int64_t chain_nsym(int64_t n, int phase);
 struct Work {
     int op = 0;
     bool cdc_both = false;            // CDC items may cover both polarisations (item.w = 2)
+    bool spectra_ready = false;       // the frames' CDC tap spectra are computed (prepared batches)
     std::vector<DevFrame> frames;
     std::vector<int4> items;          // CDC: (frame, first block, blocks)
     std::vector<AeqChain> chains;     // AEQ runs, longest first
@@ -45,7 +46,7 @@ struct Work {
     std::vector<int> item_cut;        // pipelined chunks: CDC items [item_cut[k], item_cut[k+1])
     std::vector<int> chain_cut;       //                   AEQ chains [chain_cut[k], chain_cut[k+1])
     int64_t scratch_bytes = 0;
-    size_t off_frames = 0, off_items = 0, off_chains = 0, off_init = 0, off_scratch = 0, total = 0;
+    size_t off_frames = 0, off_items = 0, off_chains = 0, off_init = 0, off_spec = 0, off_scratch = 0, total = 0;
 };
 
 constexpr size_t kStateBytes = 16 * kAeqK * sizeof(int32_t);
@@ -60,6 +61,8 @@ inline int update_period(const fnt_plan_desc &d) { return d.aeq_update_period > 
 
 fnt_status build_work(const fnt_plan *p, const fnt_frame_batch *b, int op, Work &w);
 void layout(Work &w);
+// Points every CDC frame's tap-spectrum slot into the allocation at dev.
+void point_spectra(Work &w, char *dev);
 fnt_status upload_work(Work &w, char *dev, cudaStream_t stream);
 // stages: bit 0 = CDC kernel, bit 1 = AEQ kernel
 fnt_status launch_work(const fnt_plan *p, const Work &w, const char *dev, cudaStream_t stream, int stages = 3);
@@ -75,6 +78,7 @@ int cdc_mults_per_block();
 int cdc_butterflies_per_block();
 int aeq_mults_per_block(int na);
 cudaError_t cdc_configure();
+cudaError_t cdc_spectra_launch(const DevFrame *frames, int n_frames, cudaStream_t stream);
 cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, bool both, int warps, int grid,
                        cudaStream_t stream);
 size_t aeq_smem_bytes(int na, int warps, int period);

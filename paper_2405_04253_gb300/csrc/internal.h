@@ -13,7 +13,7 @@ constexpr int kBlocksPerItem = 32; // CDC blocks per warp work item (one per lan
 // CDC work item: int4 (frame, first block, blocks, polarisation); a group of 32
 // blocks of an n_pol = 2 frame is two consecutive items (pol 0, pol 1).
 
-// One frame as the kernels see it (128 bytes, 16-byte aligned).
+// One frame as the kernels see it (16-byte aligned).
 struct alignas(16) DevFrame {
     const int8_t *in;      // CDC / chain: int8 [n][n_pol][2]; AEQ alone: int8 [n][4]
     void *out;             // CDC: int16 [n][n_pol][2]; chain / AEQ: int16 [n_sym][4]
@@ -27,9 +27,11 @@ struct alignas(16) DevFrame {
     int32_t shift;         // CDC -> AEQ requantisation shift s_c
     int32_t phase;         // decimation phase
     int32_t pad0;
+    int32_t *hspec;        // CDC tap spectra H_u [64], H_v [64] (cdc_spectra_kernel writes them)
     int8_t taps[64];       // [L][2] (re, im), zero beyond L
 };
-static_assert(sizeof(DevFrame) == 128 + 0 || sizeof(DevFrame) % 16 == 0, "DevFrame layout");
+static_assert(sizeof(DevFrame) % 16 == 0 && sizeof(DevFrame) <= 256, "DevFrame layout");
+constexpr size_t kSpecBytes = 2 * kCdcN * sizeof(int32_t);   // per frame
 
 // One AEQ run: a whole frame, or one segment of a long frame.
 struct alignas(16) AeqChain {

@@ -40,7 +40,8 @@ constexpr size_t kOffFrame = 0;
 constexpr size_t kOffItems = 256;
 constexpr size_t kOffChains = kOffItems + ((size_t)kMaxItems * sizeof(int4) + 255) / 256 * 256;
 constexpr size_t kOffInit = kOffChains + ((size_t)kMaxChains * sizeof(AeqChain) + 255) / 256 * 256;
-constexpr size_t kOffSym = kOffInit + (kStateBytes + 255) / 256 * 256;
+constexpr size_t kOffSpec = kOffInit + (kStateBytes + 255) / 256 * 256;
+constexpr size_t kOffSym = kOffSpec + (kSpecBytes + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kOffSym + (size_t)kMaxSym * 4;
 
 constexpr int kMaxDevices = 64;
@@ -49,7 +50,7 @@ constexpr int kMaxDevices = 64;
 }  // namespace fnt
 
 // The scratch: frame descriptor, CDC work items, AEQ chains, a copy of the
-// initial taps, intermediate symbols.
+// initial taps, the CDC tap spectra, intermediate symbols.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[fnt::kScratchBytes];
 
 namespace fnt {
@@ -114,6 +115,7 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
     df.in = (const int8_t *)f->in;
     df.out = f->out;
     df.aeq_in = (int8_t *)(base + kOffSym);
+    df.hspec = (int32_t *)(base + kOffSpec);
     df.state = f->aeq_state;
     df.n = f->n;
     df.n_sym = nsym;
@@ -163,6 +165,8 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
 
     const DevFrame *frames = (const DevFrame *)(base + kOffFrame);
     const int nw = p->cdc_warps;
+    e = cdc_spectra_launch(frames, 1, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "noalloc: tap spectra launch");
     e = cdc_launch(frames, (const int4 *)(base + kOffItems), n_items, true, false, nw,
                    std::min((n_items + nw - 1) / nw, p->n_sm * 64), stream);
     if (e != cudaSuccess) return cuda_fail(e, "noalloc: cdc kernel launch");

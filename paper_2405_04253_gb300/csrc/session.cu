@@ -252,6 +252,7 @@ fnt_status launch_wave(fnt_session *ss, Slot &slot) {
     const size_t bytes = off_copies + copies.size() * sizeof(StateCopy);
     fnt_status st = grow(slot, bytes);
     if (st != FNT_OK) return st;
+    point_spectra(w, slot.d_tables);              // after grow: the tables may have moved
     memcpy(slot.h_tables + w.off_frames, w.frames.data(), w.frames.size() * sizeof(DevFrame));
     if (!w.items.empty()) memcpy(slot.h_tables + w.off_items, w.items.data(), w.items.size() * sizeof(int4));
     if (!w.chains.empty())
