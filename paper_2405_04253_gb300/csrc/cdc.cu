@@ -134,7 +134,6 @@ __global__ void __launch_bounds__(128, BOTH ? 2 : 3) cdc_kernel(const DevFrame *
         const int nb = item.z;
         const int pol = item.w;                       // polarisation this warp computes, 2 = both
         const int S = fr.S;
-        const int L = fr.L;
         const int npol = fr.n_pol;
         const int64_t n = fr.n;
 

@@ -76,8 +76,6 @@ class Arena {
             }
         }
     }
-    size_t used() const { return used_; }
-
    private:
     size_t cap_;
     size_t used_ = 0;
