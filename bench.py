@@ -609,7 +609,6 @@ def run_cfg4(args):
     plans = {"serial": dict(), "segmented": dict(aeq_segment=1024, aeq_warmup=0)}
 
     def serve(paced: bool, plan):
-        from collections import deque
         sess = fnt.Session(plan, len(tr.link_taps), 8 << 30, args.streams)
         for l, t in enumerate(tr.link_taps):
             sess.set_link(l, t)
@@ -618,31 +617,36 @@ def run_cfg4(args):
             xh = torch.from_numpy(f.x).pin_memory()
             oh = torch.zeros((fnt.chain_nsym(f.x.shape[0], f.taps.shape[0]), 4), dtype=torch.int16).pin_memory()
             bufs.append((xh, oh))
+        # request records are prepared with the buffers; arrivals are admitted in
+        # arrival order, all frames that have arrived in one call
+        reqs = fnt.Requests([f.link for f in tr.frames], [b[0] for b in bufs], [b[1] for b in bufs])
+        arrival = np.array([f.arrival_s for f in tr.frames])
         n = len(tr.frames)
-        submitted, lat, status = {}, [], []
-        waiting = deque()
-        i = completed = 0
+        t_ref = np.zeros(n + 1)                 # per ticket (tickets count up from 1)
+        lat, status = [], []
+        i = adm = completed = 0
         t_first = t_last = None
         t0 = time.perf_counter()
         while completed < n:
             now = time.perf_counter() - t0
-            while i < n and (not paced or tr.frames[i].arrival_s <= now):
-                waiting.append(i)
-                i += 1
-            while waiting:
-                j = waiting[0]
-                tk = sess.try_submit(tr.frames[j].link, bufs[j][0], bufs[j][1])
-                if tk is None:
-                    break                                   # memory cap reached: keep arrival order
-                waiting.popleft()
-                t_ref = tr.frames[j].arrival_s if paced else time.perf_counter() - t0
-                t_first = t_ref if t_first is None else min(t_first, t_ref)
-                submitted[tk] = t_ref
-            for c in sess.poll(timeout_us=0):
+            if paced:
+                while i < n and arrival[i] <= now:
+                    i += 1
+            else:
+                i = n
+            if adm < i:
+                tks = sess.submit_many(reqs, start=adm, count=i - adm)   # stops where the cap refuses
+                if tks:
+                    t_sub = arrival[adm:adm + len(tks)] if paced else np.full(len(tks), time.perf_counter() - t0)
+                    t_ref[tks] = t_sub
+                    t_first = float(t_sub.min()) if t_first is None else min(t_first, float(t_sub.min()))
+                    adm += len(tks)
+            got = sess.poll_array(timeout_us=0)
+            if len(got):
                 t_done = time.perf_counter() - t0
-                lat.append((t_done - submitted.pop(c["ticket"])) * 1e3)
-                status.append(c["status"])
-                completed += 1
+                lat.extend(((t_done - t_ref[got["ticket"].astype(np.int64)]) * 1e3).tolist())
+                status.extend(got["status"].tolist())
+                completed += len(got)
                 t_last = t_done
         sess.close()
         samples = sum(f.x.shape[0] for f in tr.frames)

@@ -330,9 +330,15 @@ FNT_API fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *plan, const fnt_frame
  * link's frames to the next (frames of a link run in submission order; the
  * delay line does not carry).  Requests are admitted while the session's device
  * memory for them (intermediate CDC -> AEQ symbols, state copies) stays within
- * mem_cap_bytes; the scheduler packs ready frames of
- * idle links into waves and runs up to n_streams waves at once, so requests
- * admitted while others run overlap with them on the device.  A plan with AEQ
+ * mem_cap_bytes.  The scheduler packs admitted frames into waves (at most one
+ * frame per link).  The oldest frame of every link with nothing on the device
+ * goes into a wave on one of n_streams main streams, so waves of unrelated links
+ * run concurrently.  While a link's previous frame is still on the device, its
+ * next frame goes into a chained wave (with the next frames of the other links
+ * whose latest frame is in that same wave) on one of 4 * n_streams further
+ * streams, which waits on the device for that one wave: the host never has to
+ * observe a completion before launching a link's next frame, and a waiting frame
+ * holds no main stream.  A plan with AEQ
  * segments cuts a long frame into segments that start from the link's taps as
  * the frame began (as fnt_cdc_aeq_run does with a frame state); the last
  * segment writes the link's taps.
@@ -364,6 +370,24 @@ FNT_API fnt_status fnt_session_set_link(fnt_session *s, int32_t link, const int8
  * request does not fit under the memory cap right now. */
 FNT_API fnt_status fnt_session_submit(fnt_session *s, int32_t link, const void *in, int64_t n, void *out,
                               uint64_t *ticket);
+
+/* One request of fnt_session_submit_many: the arguments of fnt_session_submit. */
+typedef struct fnt_request {
+    int32_t link;
+    int32_t reserved;        /* must be 0 */
+    const void *in;          /* int8 [n][2][2] */
+    int64_t n;               /* samples per polarisation */
+    void *out;               /* int16 [n_sym][4] */
+} fnt_request;
+
+/* Admits reqs[0..n_reqs) in order, each exactly as fnt_session_submit would,
+ * then runs the scheduler once, so a burst of requests forms full waves with
+ * one call.  Stops at the first request that is not admitted and returns its
+ * status (FNT_ERR_BUSY when the memory cap refuses it: poll, then submit the
+ * rest); FNT_OK when all were admitted.  *n_admitted is the number admitted and
+ * tickets[0..*n_admitted) their tickets (HOST arrays of n_reqs entries). */
+FNT_API fnt_status fnt_session_submit_many(fnt_session *s, const fnt_request *reqs, int32_t n_reqs,
+                                   uint64_t *tickets, int32_t *n_admitted);
 
 /* Drives the scheduler and collects finished requests (at most max_done).  Waits
  * up to timeout_us for at least one completion (0 = do not wait); returns

@@ -58,6 +58,15 @@ class Completion(ctypes.Structure):
                 ("done_us", ctypes.c_double)]
 
 
+# fnt_request (batched session admission) and fnt_completion as numpy records
+REQUEST_DTYPE = np.dtype([("link", np.int32), ("reserved", np.int32), ("in_", np.uint64), ("n", np.int64),
+                          ("out", np.uint64)], align=True)
+COMPLETION_DTYPE = np.dtype([("ticket", np.uint64), ("link", np.int32), ("status", np.int32), ("n_sym", np.int64),
+                             ("submit_us", np.float64), ("start_us", np.float64), ("done_us", np.float64)],
+                            align=True)
+assert REQUEST_DTYPE.itemsize == 32 and COMPLETION_DTYPE.itemsize == ctypes.sizeof(Completion)
+
+
 # Every symbol include/fnt.h declares, with (restype, argtypes).
 _VP, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 SIGNATURES = {
@@ -83,6 +92,7 @@ SIGNATURES = {
     "fnt_session_create": (_I32, [_VP, _I32, _SZ, _I32, ctypes.POINTER(_VP)]),
     "fnt_session_set_link": (_I32, [_VP, _I32, _VP, _I32]),
     "fnt_session_submit": (_I32, [_VP, _I32, _VP, _I64, _VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "fnt_session_submit_many": (_I32, [_VP, _VP, _I32, _VP, ctypes.POINTER(_I32)]),
     "fnt_session_poll": (_I32, [_VP, _I32, ctypes.POINTER(Completion), _I32, ctypes.POINTER(_I32)]),
     "fnt_session_pending": (_I32, [_VP]),
     "fnt_session_get_link_state": (_I32, [_VP, _I32, _VP]),
@@ -273,6 +283,23 @@ def chain_nsym(n: int, L: int) -> int:
     return max(0, (n - phase + 1) // 2)
 
 
+class Requests:
+    """Prepared fnt_request records for fnt_session_submit_many: frame i goes to
+    links[i] with input xs[i] and output outs[i] (tensors or page-locked arrays,
+    kept alive here)."""
+
+    def __init__(self, links, xs, outs, ns=None):
+        self.rec = np.zeros(len(xs), REQUEST_DTYPE)
+        self.rec["link"] = np.asarray(links, dtype=np.int32)
+        self.rec["in_"] = [_ptr(x) or 0 for x in xs]
+        self.rec["n"] = [int(x.shape[0]) for x in xs] if ns is None else np.asarray(ns, dtype=np.int64)
+        self.rec["out"] = [_ptr(o) or 0 for o in outs]
+        self.bufs = list(zip(xs, outs))
+
+    def __len__(self) -> int:
+        return len(self.rec)
+
+
 class Session:
     """Continuous-batching serving session (fnt_session)."""
 
@@ -282,6 +309,7 @@ class Session:
         check(lib().fnt_session_create(plan.handle, n_links, mem_cap_bytes, n_streams, ctypes.byref(h)))
         self.handle = h
         self._keep = {}
+        self._done = np.zeros(0, COMPLETION_DTYPE)
 
     def set_link(self, link: int, taps):
         t = np.ascontiguousarray(taps, dtype=np.int8)
@@ -305,6 +333,39 @@ class Session:
         check(st)
         self._keep[tk.value] = (x, out)
         return tk.value
+
+    def submit_many(self, reqs: Requests, start: int = 0, count: int | None = None) -> list[int]:
+        """Admits reqs[start:start+count] in order with one call; returns the
+        tickets of those admitted (a prefix: admission stops where the memory
+        cap refuses a request).  Other errors raise FntError."""
+        n = len(reqs) - start if count is None else int(count)
+        if n <= 0:
+            return []
+        tk = np.zeros(n, np.uint64)
+        na = ctypes.c_int32()
+        st = lib().fnt_session_submit_many(self.handle, reqs.rec.ctypes.data + start * REQUEST_DTYPE.itemsize, n,
+                                           tk.ctypes.data, ctypes.byref(na))
+        out = tk[:na.value].tolist()
+        for i, t in enumerate(out):
+            self._keep[t] = reqs.bufs[start + i]
+        if st != FNT_ERR_BUSY:
+            check(st)
+        return out
+
+    def poll_array(self, timeout_us: int = 0, max_done: int = 4096) -> np.ndarray:
+        """As :meth:`poll`, returning the completions as a COMPLETION_DTYPE array."""
+        if self._done.shape[0] < max_done:
+            self._done = np.zeros(max_done, COMPLETION_DTYPE)
+        nd = ctypes.c_int32()
+        st = lib().fnt_session_poll(self.handle, timeout_us, self._done.ctypes.data_as(ctypes.POINTER(Completion)),
+                                    max_done, ctypes.byref(nd))
+        if st == FNT_ERR_TIMEOUT:
+            return self._done[:0].copy()
+        check(st)
+        got = self._done[:nd.value].copy()
+        for t in got["ticket"].tolist():
+            self._keep.pop(t, None)
+        return got
 
     def poll(self, timeout_us: int = 0, max_done: int = 1024):
         arr = (Completion * max_done)()

@@ -516,13 +516,14 @@ struct Staging {
             if (e != cudaSuccess) return e;
             device = dev;
         }
-        if (cap < bytes) {
+        if (cap < bytes) {                        // geometric: reallocation stays rare
+            const size_t want = std::max({bytes, 2 * cap, (size_t)64 << 10});
             if (buf) cudaFreeHost(buf);
             buf = nullptr;
             cap = 0;
-            e = cudaMallocHost((void **)&buf, bytes);
+            e = cudaMallocHost((void **)&buf, want);
             if (e != cudaSuccess) return e;
-            cap = bytes;
+            cap = want;
         }
         return cudaSuccess;
     }

@@ -5,15 +5,22 @@
 // session's device arena (capped at mem_cap bytes) can hold their buffers:
 // intermediate CDC->AEQ symbols (and, for segmented frames, a copy of the link's
 // taps).  Inputs and outputs stay where the caller put them: device memory, or
-// page-locked host memory that the kernels read and write directly.  A scheduler packs the oldest ready frame of each
-// idle link into a wave, runs the CDC and AEQ kernels for the whole wave on one
-// of n_streams streams, and records an event; up to n_streams waves run at
-// once, so requests admitted while others are on the GPU overlap with them.  A
-// link is idle while none of its frames is in flight, which keeps every link's
-// frames in submission order (its tap state is read and written by one chain at
-// a time).  With AEQ segments in the plan, a long frame's segments start from the
-// link's taps as the frame began and run in parallel; the last one writes the
-// link's taps.  Completion is observed on the host by querying the wave's event.
+// page-locked host memory that the kernels read and write directly.
+//
+// A scheduler packs admitted frames into waves, at most one frame per link, and
+// runs the CDC and AEQ kernels of a whole wave on a lane (a stream running one
+// wave at a time), recording an event after it.  The oldest frame of every link
+// with nothing on the device goes into a wave on one of n_streams main lanes.
+// The next frame of a link whose latest frame is still on the device goes into a
+// chained wave with the next frames of every other link whose latest frame is in
+// that same wave; a chained wave runs on one of kChainLanes * n_streams chain
+// lanes, whose stream first waits on the event of that one wave.  A link's frames
+// thus run in submission order and its tap state is read and written by one chain
+// at a time; the host keeps the device fed without waiting for completions; and
+// no frame waits behind an unrelated link's dependency or holds a main lane while
+// it waits.  With AEQ segments in the plan, a long frame's segments start from
+// the link's taps as the frame began and run in parallel; the last one writes the
+// link's taps.  Completion is observed on the host by querying each wave's event.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,6 +98,8 @@ struct Request {
     int64_t n_sym = 0;
     size_t off = 0, bytes = 0;    // arena reservation
     size_t off_scratch = 0, off_init = 0;
+    uint64_t prev_wave = 0;       // the link's latest in-flight frame before this one:
+    int prev_wi = -1;             // id and pool index of its wave
     double submit_us = 0, start_us = 0;
 };
 
@@ -99,21 +108,32 @@ struct LinkState {
     int L = 0;
     int8_t taps[64] = {0};
     int shift = 0, phase = 0, S = 0;
-    bool busy = false;           // a frame of this link is in flight
+    int inflight = 0;            // frames of this link launched and not yet completed
+    uint64_t last_wave = 0;      // id and pool index of the wave holding its latest
+    int last_wi = -1;            // in-flight frame (-1: nothing on the device)
     std::deque<Request> fifo;    // admitted, not yet launched
 };
 
-struct Slot {
-    cudaStream_t stream = nullptr;
+// One wave: its requests, device work tables (and their page-locked staging)
+// and the event recorded after its kernels.
+struct Wave {
+    uint64_t id = 0;
     cudaEvent_t done = nullptr;
-    bool busy = false;
-    char *d_tables = nullptr;    // device work tables of the slot's wave
+    char *d_tables = nullptr;
     size_t d_cap = 0;
-    char *h_tables = nullptr;    // page-locked staging of the same
+    char *h_tables = nullptr;
     size_t h_cap = 0;
     std::vector<Request> reqs;
-    int status = FNT_OK;
 };
+
+// A stream running at most one wave (index into the wave pool) at a time.
+struct Lane {
+    cudaStream_t stream = nullptr;
+    int wave = -1;
+};
+
+constexpr int kChainLanes = 4;   // chain lanes per main lane
+constexpr size_t kInitialTables = 64 << 10;   // a wave's first table allocation
 
 }  // namespace
 }  // namespace fnt
@@ -128,7 +148,12 @@ struct fnt_session {
     Arena arena{0};
     int32_t *d_state = nullptr;           // [n_links][16][K]
     std::vector<LinkState> links;
-    std::vector<Slot> slots;
+    int n_main = 0;
+    std::vector<Lane> lanes;              // n_main main lanes, then the chain lanes
+    std::vector<Wave> waves;              // one per lane
+    std::vector<int> free_waves;
+    uint64_t next_wave = 1;
+    std::vector<char *> retired;          // outgrown table staging, freed at destroy
     std::deque<fnt_completion> done;
     uint64_t next_ticket = 1;
     int admitted = 0;                     // admitted and not yet returned by poll
@@ -161,15 +186,20 @@ size_t request_bytes(const fnt_plan *p, const Request &r) {
     return b;
 }
 
-fnt_status grow(Slot &s, size_t bytes) {
+// Makes room for `bytes` of tables in a wave object, without a device-wide
+// synchronisation (which cudaFree would imply, stalling every wave in flight):
+// device tables come from the plan's stream-ordered pool on the stream about to
+// use them, and an outgrown page-locked staging buffer is kept until the session
+// is destroyed.  The wave object is free, so nothing in flight uses either.
+fnt_status grow(fnt_session *ss, Wave &s, size_t bytes, cudaStream_t stream) {
     if (bytes <= s.d_cap) return FNT_OK;
-    size_t cap = std::max(bytes, s.d_cap * 2);
-    if (s.d_tables) cudaFree(s.d_tables);
-    if (s.h_tables) cudaFreeHost(s.h_tables);
+    const size_t cap = std::max({bytes, s.d_cap * 2, kInitialTables});
+    if (s.d_tables) cudaFreeAsync(s.d_tables, stream);
+    if (s.h_tables) ss->retired.push_back(s.h_tables);
     s.d_tables = nullptr;
     s.h_tables = nullptr;
     s.d_cap = s.h_cap = 0;
-    cudaError_t e = cudaMalloc(&s.d_tables, cap);
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&s.d_tables, cap, ss->plan->pool, stream);
     if (e != cudaSuccess) return cuda_fail(e, "session: table memory");
     e = cudaMallocHost(&s.h_tables, cap);
     if (e != cudaSuccess) return cuda_fail(e, "session: table staging");
@@ -177,19 +207,20 @@ fnt_status grow(Slot &s, size_t bytes) {
     return FNT_OK;
 }
 
-// Builds the wave's tables in the slot's staging memory and enqueues copies,
-// kernels and result copies on the slot's stream.
-fnt_status launch_wave(fnt_session *ss, Slot &slot) {
+// Builds the wave's tables in its staging memory and enqueues on `stream`: a wait
+// for `dep` (if not null), the table upload, the state copies, the kernels and
+// the wave's event.
+fnt_status launch_wave(fnt_session *ss, cudaStream_t stream, Wave &wave, cudaEvent_t dep) {
     if (ss->inject_failures > 0) {
         --ss->inject_failures;
         return fail(FNT_ERR_CUDA, "session: injected wave failure");
     }
     Work w;
     w.op = FNT_OP_CHAIN;
-    const int nf = (int)slot.reqs.size();
+    const int nf = (int)wave.reqs.size();
     w.frames.resize(nf);
     for (int i = 0; i < nf; ++i) {
-        const Request &r = slot.reqs[i];
+        const Request &r = wave.reqs[i];
         const LinkState &lk = ss->links[r.link];
         DevFrame &df = w.frames[i];
         memset(&df, 0, sizeof df);
@@ -243,38 +274,50 @@ fnt_status launch_wave(fnt_session *ss, Slot &slot) {
     w.chain_cut = {0, (int)w.chains.size()};
     layout(w);
     std::vector<StateCopy> copies;
-    for (const Request &r : slot.reqs)
+    for (const Request &r : wave.reqs)
         if (segmented(ss->plan, r.n_sym))
             copies.push_back({ss->d_state + (size_t)r.link * 16 * kAeqK, (int32_t *)(ss->arena_mem + r.off_init)});
     const size_t off_copies = w.total;
     const size_t bytes = off_copies + copies.size() * sizeof(StateCopy);
-    fnt_status st = grow(slot, bytes);
+    fnt_status st = grow(ss, wave, bytes, stream);
     if (st != FNT_OK) return st;
-    point_spectra(w, slot.d_tables);              // after grow: the tables may have moved
-    memcpy(slot.h_tables + w.off_frames, w.frames.data(), w.frames.size() * sizeof(DevFrame));
-    if (!w.items.empty()) memcpy(slot.h_tables + w.off_items, w.items.data(), w.items.size() * sizeof(int4));
+    point_spectra(w, wave.d_tables);              // after grow: the tables may have moved
+    memcpy(wave.h_tables + w.off_frames, w.frames.data(), w.frames.size() * sizeof(DevFrame));
+    if (!w.items.empty()) memcpy(wave.h_tables + w.off_items, w.items.data(), w.items.size() * sizeof(int4));
     if (!w.chains.empty())
-        memcpy(slot.h_tables + w.off_chains, w.chains.data(), w.chains.size() * sizeof(AeqChain));
-    if (!copies.empty()) memcpy(slot.h_tables + off_copies, copies.data(), copies.size() * sizeof(StateCopy));
-    cudaError_t e = cudaMemcpyAsync(slot.d_tables, slot.h_tables, bytes, cudaMemcpyHostToDevice, slot.stream);
+        memcpy(wave.h_tables + w.off_chains, w.chains.data(), w.chains.size() * sizeof(AeqChain));
+    if (!copies.empty()) memcpy(wave.h_tables + off_copies, copies.data(), copies.size() * sizeof(StateCopy));
+    cudaError_t e = dep ? cudaStreamWaitEvent(stream, dep, 0) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(e, "session: wave dependency");
+    e = cudaMemcpyAsync(wave.d_tables, wave.h_tables, bytes, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return cuda_fail(e, "session: table upload");
     if (!copies.empty()) {
-        copy_states<<<std::min<int>((int)copies.size(), 1024), 256, 0, slot.stream>>>(
-            (const StateCopy *)(slot.d_tables + off_copies), (int)copies.size());
+        copy_states<<<std::min<int>((int)copies.size(), 1024), 256, 0, stream>>>(
+            (const StateCopy *)(wave.d_tables + off_copies), (int)copies.size());
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "session: state copy launch");
     }
-    st = launch_work(ss->plan, w, slot.d_tables, slot.stream);
+    st = launch_work(ss->plan, w, wave.d_tables, stream);
     if (st != FNT_OK) return st;
-    e = cudaEventRecord(slot.done, slot.stream);
+    e = cudaEventRecord(wave.done, stream);
     if (e != cudaSuccess) return cuda_fail(e, "session: event record");
     return FNT_OK;
 }
 
-void complete(fnt_session *ss, Slot &slot, int status, double t) {
-    for (const Request &r : slot.reqs) {
+// Returns a finished (or never launched) wave's requests as completions and the
+// wave to the pool.  A link whose latest in-flight frame was in this wave has
+// none left on the device; when the launch failed, its previous in-flight frame
+// (if any) is its latest again.
+void complete(fnt_session *ss, int wi, int status, double t, bool launch_failed) {
+    Wave &wave = ss->waves[wi];
+    for (const Request &r : wave.reqs) {
         ss->arena.release(r.off, r.bytes);
-        ss->links[r.link].busy = false;
+        LinkState &lk = ss->links[r.link];
+        --lk.inflight;
+        if (lk.last_wave == wave.id) {
+            lk.last_wave = launch_failed ? r.prev_wave : 0;
+            lk.last_wi = launch_failed ? r.prev_wi : -1;
+        }
         fnt_completion c{};
         c.ticket = r.ticket;
         c.link = r.link;
@@ -285,48 +328,122 @@ void complete(fnt_session *ss, Slot &slot, int status, double t) {
         c.done_us = t;
         ss->done.push_back(c);
     }
-    slot.reqs.clear();
-    slot.busy = false;
+    wave.reqs.clear();
+    ss->free_waves.push_back(wi);
 }
 
-// Forms and launches waves while a slot is free and a link has a ready frame.
+// Launches one wave on lane `li` holding the oldest frame of each link in
+// `ready`; its stream first waits for `dep` when that is not null.
+void form_wave(fnt_session *ss, int li, cudaEvent_t dep, std::vector<std::pair<double, int>> &ready) {
+    std::sort(ready.begin(), ready.end());
+    if ((int)ready.size() > kMaxWave) ready.resize(kMaxWave);
+    Lane &lane = ss->lanes[li];
+    const int wi = ss->free_waves.back();
+    ss->free_waves.pop_back();
+    Wave &wave = ss->waves[wi];
+    wave.id = ss->next_wave++;
+    const double t = now_us();
+    for (auto &pr : ready) {
+        LinkState &lk = ss->links[pr.second];
+        Request r = lk.fifo.front();
+        lk.fifo.pop_front();
+        r.prev_wave = lk.last_wave;
+        r.prev_wi = lk.last_wi;
+        lk.last_wave = wave.id;
+        lk.last_wi = wi;
+        ++lk.inflight;
+        r.start_us = t;
+        wave.reqs.push_back(r);
+    }
+    lane.wave = wi;
+    fnt_status st = launch_wave(ss, lane.stream, wave, dep);
+    if (st != FNT_OK) {
+        // nothing of a failed wave is trusted: its requests complete with the error
+        cudaStreamSynchronize(lane.stream);
+        lane.wave = -1;
+        complete(ss, wi, st, now_us(), true);
+    }
+}
+
+// Forms and launches waves while frames are admitted and lanes are free: frames
+// of links with nothing on the device on free main lanes; then chained waves,
+// the group waiting on the wave that holds the oldest waiting frame first.
 void schedule(fnt_session *ss) {
-    for (Slot &slot : ss->slots) {
-        if (slot.busy) continue;
-        std::vector<std::pair<double, int>> ready;
+    std::vector<std::pair<double, int>> ready;
+    const int n_lanes = (int)ss->lanes.size();
+    for (int li = 0; li < ss->n_main; ++li) {
+        if (ss->lanes[li].wave >= 0) continue;
+        ready.clear();
         for (int l = 0; l < ss->n_links; ++l) {
-            LinkState &lk = ss->links[l];
-            if (!lk.busy && !lk.fifo.empty()) ready.push_back({lk.fifo.front().submit_us, l});
+            const LinkState &lk = ss->links[l];
+            if (lk.last_wi < 0 && !lk.fifo.empty()) ready.push_back({lk.fifo.front().submit_us, l});
         }
-        if (ready.empty()) return;
-        std::sort(ready.begin(), ready.end());
-        if ((int)ready.size() > kMaxWave) ready.resize(kMaxWave);
-        const double t = now_us();
-        for (auto &pr : ready) {
-            LinkState &lk = ss->links[pr.second];
-            Request r = lk.fifo.front();
-            lk.fifo.pop_front();
-            lk.busy = true;
-            r.start_us = t;
-            slot.reqs.push_back(r);
+        if (ready.empty()) break;
+        form_wave(ss, li, nullptr, ready);
+    }
+    for (int li = ss->n_main; li < n_lanes; ++li) {
+        if (ss->lanes[li].wave >= 0) continue;
+        int dep = -1;
+        double oldest = 0;
+        for (int l = 0; l < ss->n_links; ++l) {
+            const LinkState &lk = ss->links[l];
+            if (lk.last_wi >= 0 && !lk.fifo.empty() && (dep < 0 || lk.fifo.front().submit_us < oldest)) {
+                dep = lk.last_wi;
+                oldest = lk.fifo.front().submit_us;
+            }
         }
-        slot.busy = true;
-        fnt_status st = launch_wave(ss, slot);
-        if (st != FNT_OK) {
-            // nothing of a failed wave is trusted: its requests complete with the error
-            cudaStreamSynchronize(slot.stream);
-            complete(ss, slot, st, now_us());
+        if (dep < 0) break;
+        ready.clear();
+        for (int l = 0; l < ss->n_links; ++l) {
+            const LinkState &lk = ss->links[l];
+            if (lk.last_wi == dep && !lk.fifo.empty()) ready.push_back({lk.fifo.front().submit_us, l});
         }
+        form_wave(ss, li, ss->waves[dep].done, ready);
     }
 }
 
 void reap(fnt_session *ss) {
-    for (Slot &slot : ss->slots) {
-        if (!slot.busy) continue;
-        cudaError_t e = cudaEventQuery(slot.done);
+    for (Lane &lane : ss->lanes) {
+        if (lane.wave < 0) continue;
+        cudaError_t e = cudaEventQuery(ss->waves[lane.wave].done);
         if (e == cudaErrorNotReady) continue;
-        complete(ss, slot, e == cudaSuccess ? FNT_OK : FNT_ERR_CUDA, now_us());
+        const int wi = lane.wave;
+        lane.wave = -1;
+        complete(ss, wi, e == cudaSuccess ? FNT_OK : FNT_ERR_CUDA, now_us(), false);
     }
+}
+
+// Validates and admits one request into its link's queue (caller holds the lock).
+fnt_status admit(fnt_session *ss, int32_t link, const void *in, int64_t n, void *out, uint64_t *ticket) {
+    if (link < 0 || link >= ss->n_links) return fail(FNT_ERR_NOT_FOUND, "no link %d", link);
+    LinkState &lk = ss->links[link];
+    if (!lk.configured) return fail(FNT_ERR_INVALID, "link %d has no taps", link);
+    if (n < 0 || (n > 0 && (!in || !out))) return fail(FNT_ERR_INVALID, "bad frame");
+    Request r;
+    r.link = link;
+    r.in = (const int8_t *)in;
+    r.out = out;
+    r.n = n;
+    r.n_sym = chain_nsym(n, lk.phase);
+    if (n > 0) {
+        void *din = device_view(in), *dout = device_view(out);
+        if (!din || !dout)
+            return fail(FNT_ERR_INVALID, "submit: in/out must be device memory or page-locked host memory");
+        if (((uintptr_t)din % 4) || ((uintptr_t)dout % 4)) return fail(FNT_ERR_INVALID, "submit: 4-byte alignment");
+        r.in = (const int8_t *)din;
+        r.out = dout;
+    }
+    r.bytes = std::max<size_t>(256, request_bytes(ss->plan, r));
+    if (r.bytes > ss->cap) return fail(FNT_ERR_BOUND, "submit: frame needs %zu bytes > cap %zu", r.bytes, ss->cap);
+    if (!ss->arena.alloc(r.bytes, r.off)) return fail(FNT_ERR_BUSY, "submit: memory cap reached");
+    r.off_scratch = r.off;
+    r.off_init = r.off + up256((size_t)r.n_sym * 4);
+    r.ticket = ss->next_ticket++;
+    r.submit_us = now_us();
+    lk.fifo.push_back(r);
+    ++ss->admitted;
+    *ticket = r.ticket;
+    return FNT_OK;
 }
 
 }  // namespace
@@ -358,10 +475,13 @@ extern "C" fnt_status fnt_session_create(const fnt_plan *plan, int32_t n_links, 
     std::vector<int32_t> init((size_t)n_links * 16 * kAeqK);
     for (int l = 0; l < n_links; ++l) memcpy(&init[(size_t)l * 16 * kAeqK], plan->h_init, sizeof plan->h_init);
     cudaMemcpy(ss->d_state, init.data(), init.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    ss->slots.resize(n_streams);
-    for (Slot &s : ss->slots) {
-        cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
-        cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    ss->n_main = n_streams;
+    ss->lanes.resize((size_t)n_streams * (1 + kChainLanes));
+    for (Lane &l : ss->lanes) cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking);
+    ss->waves.resize(ss->lanes.size());
+    for (int i = (int)ss->waves.size() - 1; i >= 0; --i) {
+        cudaEventCreateWithFlags(&ss->waves[i].done, cudaEventDisableTiming);
+        ss->free_waves.push_back(i);
     }
     *out = ss;
     return FNT_OK;
@@ -372,7 +492,7 @@ extern "C" fnt_status fnt_session_set_link(fnt_session *ss, int32_t link, const 
     std::lock_guard<std::mutex> g(ss->mu);
     if (link < 0 || link >= ss->n_links) return fail(FNT_ERR_NOT_FOUND, "no link %d", link);
     LinkState &lk = ss->links[link];
-    if (lk.busy || !lk.fifo.empty()) return fail(FNT_ERR_BUSY, "link %d has requests in the session", link);
+    if (lk.inflight || !lk.fifo.empty()) return fail(FNT_ERR_BUSY, "link %d has requests in the session", link);
     if (!taps || L < 1) return fail(FNT_ERR_INVALID, "link %d: no taps", link);
     if (L > kMaxCdTaps) return fail(FNT_ERR_BOUND, "link %d: %d taps > %d (constraint (5))", link, L, kMaxCdTaps);
     for (int k = 0; k < 2 * L; ++k)
@@ -396,36 +516,26 @@ extern "C" fnt_status fnt_session_submit(fnt_session *ss, int32_t link, const vo
                                          uint64_t *ticket) {
     if (!ss || !ticket) return fail(FNT_ERR_INVALID, "null argument");
     std::lock_guard<std::mutex> g(ss->mu);
-    if (link < 0 || link >= ss->n_links) return fail(FNT_ERR_NOT_FOUND, "no link %d", link);
-    LinkState &lk = ss->links[link];
-    if (!lk.configured) return fail(FNT_ERR_INVALID, "link %d has no taps", link);
-    if (n < 0 || (n > 0 && (!in || !out))) return fail(FNT_ERR_INVALID, "bad frame");
-    Request r;
-    r.link = link;
-    r.in = (const int8_t *)in;
-    r.out = out;
-    r.n = n;
-    r.n_sym = chain_nsym(n, lk.phase);
-    if (n > 0) {
-        void *din = device_view(in), *dout = device_view(out);
-        if (!din || !dout)
-            return fail(FNT_ERR_INVALID, "submit: in/out must be device memory or page-locked host memory");
-        if (((uintptr_t)din % 4) || ((uintptr_t)dout % 4)) return fail(FNT_ERR_INVALID, "submit: 4-byte alignment");
-        r.in = (const int8_t *)din;
-        r.out = dout;
+    fnt_status st = admit(ss, link, in, n, out, ticket);
+    if (st == FNT_OK) schedule(ss);
+    return st;
+}
+
+extern "C" fnt_status fnt_session_submit_many(fnt_session *ss, const fnt_request *reqs, int32_t n_reqs,
+                                              uint64_t *tickets, int32_t *n_admitted) {
+    if (!ss || !n_admitted || n_reqs < 0 || (n_reqs > 0 && (!reqs || !tickets)))
+        return fail(FNT_ERR_INVALID, "bad argument");
+    *n_admitted = 0;
+    std::lock_guard<std::mutex> g(ss->mu);
+    fnt_status st = FNT_OK;
+    for (int32_t i = 0; i < n_reqs && st == FNT_OK; ++i) {
+        const fnt_request &q = reqs[i];
+        st = q.reserved ? fail(FNT_ERR_INVALID, "request %d: reserved field not 0", i)
+                        : admit(ss, q.link, q.in, q.n, q.out, &tickets[i]);
+        if (st == FNT_OK) ++*n_admitted;
     }
-    r.bytes = std::max<size_t>(256, request_bytes(ss->plan, r));
-    if (r.bytes > ss->cap) return fail(FNT_ERR_BOUND, "submit: frame needs %zu bytes > cap %zu", r.bytes, ss->cap);
-    if (!ss->arena.alloc(r.bytes, r.off)) return fail(FNT_ERR_BUSY, "submit: memory cap reached");
-    r.off_scratch = r.off;
-    r.off_init = r.off + up256((size_t)r.n_sym * 4);
-    r.ticket = ss->next_ticket++;
-    r.submit_us = now_us();
-    lk.fifo.push_back(r);
-    ++ss->admitted;
-    *ticket = r.ticket;
-    schedule(ss);
-    return FNT_OK;
+    if (*n_admitted > 0) schedule(ss);
+    return st;
 }
 
 extern "C" fnt_status fnt_session_poll(fnt_session *ss, int32_t timeout_us, fnt_completion *done, int32_t max_done,
@@ -456,7 +566,7 @@ extern "C" int32_t fnt_session_pending(const fnt_session *ss) { return ss ? ss->
 static fnt_status link_idle(fnt_session *ss, int32_t link) {
     if (link < 0 || link >= ss->n_links) return fail(FNT_ERR_NOT_FOUND, "no link %d", link);
     const LinkState &lk = ss->links[link];
-    if (lk.busy || !lk.fifo.empty()) return fail(FNT_ERR_BUSY, "link %d has requests in the session", link);
+    if (lk.inflight || !lk.fifo.empty()) return fail(FNT_ERR_BUSY, "link %d has requests in the session", link);
     return FNT_OK;
 }
 
@@ -496,19 +606,23 @@ extern "C" fnt_status fnt_session_destroy(fnt_session *ss) {
             std::lock_guard<std::mutex> g(ss->mu);
             reap(ss);
             schedule(ss);
-            for (const Slot &s : ss->slots) idle = idle && !s.busy;
+            for (const Lane &l : ss->lanes) idle = idle && l.wave < 0;
             for (const LinkState &lk : ss->links) idle = idle && lk.fifo.empty();
         }
         if (idle) break;
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    for (Slot &s : ss->slots) {
-        if (s.stream) cudaStreamSynchronize(s.stream);
-        if (s.done) cudaEventDestroy(s.done);
-        if (s.stream) cudaStreamDestroy(s.stream);
-        if (s.d_tables) cudaFree(s.d_tables);
-        if (s.h_tables) cudaFreeHost(s.h_tables);
+    for (Lane &l : ss->lanes) {
+        if (!l.stream) continue;
+        cudaStreamSynchronize(l.stream);
+        cudaStreamDestroy(l.stream);
     }
+    for (Wave &w : ss->waves) {
+        if (w.done) cudaEventDestroy(w.done);
+        if (w.d_tables) cudaFree(w.d_tables);
+        if (w.h_tables) cudaFreeHost(w.h_tables);
+    }
+    for (char *h : ss->retired) cudaFreeHost(h);
     cudaFree(ss->arena_mem);
     cudaFree(ss->d_state);
     delete ss;

@@ -218,3 +218,123 @@ def test_session_segmented_plan_matches_sequential_oracle(orc, period):
         assert np.array_equal(got[i], ref), i
     for l in range(len(links)):
         assert np.array_equal(Tgot[l], T[l])
+
+
+def _device_frames(frames, links, host=False):
+    xs, outs = [], []
+    for link, x in frames:
+        nsym = F.chain_nsym(x.shape[0], links[link].shape[0])
+        if host:
+            xs.append(torch.from_numpy(x).pin_memory())
+            outs.append(torch.zeros((nsym, 4), dtype=torch.int16).pin_memory())
+        else:
+            xs.append(torch.from_numpy(x).cuda())
+            outs.append(torch.zeros((nsym, 4), dtype=torch.int16, device="cuda"))
+    torch.cuda.synchronize()
+    return xs, outs
+
+
+def _drain(s, n):
+    got = []
+    while len(got) < n:
+        got.extend(s.poll_array(timeout_us=1000000).tolist())
+    return got
+
+
+@pytest.mark.parametrize("streams,host", [(4, False), (2, True), (8, False)])
+def test_session_submit_many_chains_links_on_device(orc, streams, host):
+    """A burst admitted with one call: every link's frames are queued behind one
+    another on the device (several per link in flight at once) and still give
+    the sequential oracle's bits and final taps."""
+    rng = np.random.default_rng(27)
+    links = make_links(rng, 5)
+    frames = make_frames(rng, 5, 6)
+    ref, Tref = oracle_sequential(orc, links, frames)
+    s = F.Session(F.Plan(mu_shift=MU), len(links), 1 << 30, streams)
+    for l, taps in enumerate(links):
+        s.set_link(l, taps)
+    xs, outs = _device_frames(frames, links, host)
+    reqs = F.Requests([l for l, _ in frames], xs, outs)
+    tk = s.submit_many(reqs)
+    assert len(tk) == len(frames) and len(set(tk)) == len(frames)
+    done = _drain(s, len(frames))
+    assert all(c[2] == F.FNT_OK for c in done)
+    for i in range(len(frames)):
+        assert np.array_equal(outs[i].cpu().numpy(), ref[i]), i
+    for l in range(len(links)):
+        assert np.array_equal(s.get_link_state(l), Tref[l])
+    s.close()
+
+
+def test_session_next_frame_launches_before_previous_completes(orc):
+    """With n_streams waves, n_streams frames of ONE link are all launched by the
+    admitting call, before any completion is observed: the order between them
+    is kept on the device."""
+    rng = np.random.default_rng(28)
+    links = make_links(rng, 1)
+    frames = [(0, rng.integers(-16, 16, (20000, 2, 2)).astype(np.int8)) for _ in range(4)]
+    ref, Tref = oracle_sequential(orc, links, frames)
+    s = F.Session(F.Plan(mu_shift=MU), 1, 1 << 30, 4)
+    s.set_link(0, links[0])
+    xs, outs = _device_frames(frames, links)
+    tk = s.submit_many(F.Requests([0] * 4, xs, outs))
+    done = sorted(_drain(s, 4))                      # by ticket
+    assert [c[0] for c in done] == tk
+    starts = [c[5] for c in done]
+    assert max(starts) < min(c[6] for c in done)
+    for i in range(4):
+        assert np.array_equal(outs[i].cpu().numpy(), ref[i]), i
+    assert np.array_equal(s.get_link_state(0), Tref[0])
+    s.close()
+
+
+def test_session_failed_wave_between_chained_frames(orc):
+    """Frame 1 in flight, frame 2's wave fails at launch, frame 3 queued behind
+    frame 1 on the device: frames 1 and 3 equal the oracle run over frames 1, 3."""
+    rng = np.random.default_rng(29)
+    links = make_links(rng, 1)
+    frames = [(0, rng.integers(-16, 16, (30000, 2, 2)).astype(np.int8)) for _ in range(3)]
+    s = F.Session(F.Plan(mu_shift=MU), 1, 1 << 30, 2)
+    s.set_link(0, links[0])
+    xs, outs = _device_frames(frames, links)
+    t1 = s.submit(0, xs[0], outs[0])
+    s.inject_failures(1)
+    t2 = s.submit(0, xs[1], outs[1])
+    t3 = s.submit(0, xs[2], outs[2])
+    res = {c[0]: c[2] for c in _drain(s, 3)}
+    assert res == {t1: F.FNT_OK, t2: F.FNT_ERR_CUDA, t3: F.FNT_OK}
+    ref, Tref = oracle_sequential(orc, links, [frames[0], frames[2]])
+    assert np.array_equal(outs[0].cpu().numpy(), ref[0])
+    assert np.array_equal(outs[2].cpu().numpy(), ref[1])
+    assert np.array_equal(s.get_link_state(0), Tref[0])
+    s.close()
+
+
+def test_session_submit_many_stops_at_cap_and_bad_request():
+    rng = np.random.default_rng(30)
+    links = make_links(rng, 2)
+    s = F.Session(F.Plan(mu_shift=MU), 2, 64 * 1024, 1)
+    for l, t in enumerate(links):
+        s.set_link(l, t)
+    x = torch.from_numpy(rng.integers(-16, 16, (20000, 2, 2)).astype(np.int8)).cuda()
+    o = [torch.zeros((F.chain_nsym(20000, links[l].shape[0]), 4), dtype=torch.int16, device="cuda")
+         for l in (0, 1, 0)]
+    reqs = F.Requests([0, 1, 0], [x, x, x], o)
+    tk = s.submit_many(reqs)                          # 40 KB each under a 64 KB cap: one fits
+    assert len(tk) == 1
+    _drain(s, 1)
+    tk2 = s.submit_many(reqs, start=1)
+    assert len(tk2) == 1 and tk2[0] > tk[0]
+    _drain(s, 1)
+    bad = F.Requests([0, 5], [x, x], [o[0], o[1]])
+    with pytest.raises(F.FntError) as e:
+        s.submit_many(bad)
+    assert e.value.status == F.FNT_ERR_NOT_FOUND
+    assert s.pending() == 1                           # the valid prefix was admitted
+    _drain(s, 1)
+    bad.rec["reserved"][0] = 1
+    with pytest.raises(F.FntError) as e:
+        s.submit_many(bad)
+    assert e.value.status == F.FNT_ERR_INVALID and s.pending() == 0
+    assert s.submit_many(reqs, start=3) == []
+    s.close()
