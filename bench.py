@@ -335,10 +335,14 @@ def run_fnt(args, rank, world, local_rank):
 
     # End to end through the public API with the stream's samples in page-locked
     # host memory: a prepared batch per host buffer (fnt_batch_create with
-    # host_buffers = 1, replayed as a graph), the kernels reading the input and
-    # writing the result in host memory, the host waiting for and reading the
-    # result every step.  The steps rotate over enough buffers (in + out more
-    # than twice the 129 MB L2) that every step's input crosses the host link.
+    # host_buffers = 1, replayed as a graph), the host waiting for and reading the
+    # result every step.  The batches copy their input to the device by DMA on
+    # their own stream, started at launch (fnt_batch_set_input_copy), so a step's
+    # input crosses the host link while the previous step computes; the kernels
+    # write the result in host memory.  The steps rotate over enough buffers (in +
+    # out more than twice the 129 MB L2) that every step's input and output cross
+    # the host link.  The in-place form (kernels reading the input across the
+    # link) is timed the same way for comparison.
     e2e = None
     if args.e2e_steps > 0:
         per_step = int(x_np.nbytes) + nsym * 8
@@ -348,31 +352,43 @@ def run_fnt(args, rank, world, local_rank):
         st_e2e = torch.from_numpy(state_snap).to(dev)
         rb = [fnt.Batch(plan, [fnt.Frame(xh[r], oh[r], taps, st_e2e)], fnt.OP_CHAIN, use_graph=True, host=True)
               for r in range(ring_h)]
-        for r in range(ring_h):
-            rb[r].launch(stream)
-        stream.synchronize()
         steps_e2e = max(args.e2e_steps, 2 * ring_h)
-        done = [torch.cuda.Event() for _ in range(steps_e2e)]
-        barrier()
-        t0 = time.perf_counter()
-        rb[0].launch(stream)
-        done[0].record(stream)
-        for k in range(steps_e2e):
-            # one step queued ahead (its buffers are the next ring slot), then
-            # wait for step k and read its result
-            if k + 1 < steps_e2e:
-                rb[(k + 1) % ring_h].launch(stream)
-                done[k + 1].record(stream)
-            done[k].synchronize()
-            _ = int(oh[k % ring_h][nsym - 1, 3])         # the host reads the step's result
-        el = reduce_max(time.perf_counter() - t0, dev)
+
+        def e2e_run(copy_in: bool) -> float:
+            for b_ in rb:
+                b_.set_input_copy(copy_in)
+            for r in range(ring_h):
+                rb[r].launch(stream)
+            stream.synchronize()
+            done = [torch.cuda.Event() for _ in range(steps_e2e)]
+            barrier()
+            t0 = time.perf_counter()
+            rb[0].launch(stream)
+            done[0].record(stream)
+            for k in range(steps_e2e):
+                # one step queued ahead (its buffers are the next ring slot), then
+                # wait for step k and read its result
+                if k + 1 < steps_e2e:
+                    rb[(k + 1) % ring_h].launch(stream)
+                    done[k + 1].record(stream)
+                done[k].synchronize()
+                _ = int(oh[k % ring_h][nsym - 1, 3])         # the host reads the step's result
+            return reduce_max(time.perf_counter() - t0, dev)
+
+        el_inplace = e2e_run(False)
+        el = e2e_run(True)
         e2e = {"value": aggregate(n * steps_e2e, world, el), "unit": UNIT,
                "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(nsym * 8),
                "ms_per_step": el / steps_e2e * 1e3, "steps": steps_e2e,
-               "api": "fnt_batch_create(host_buffers=1) once per buffer; per step fnt_batch_launch, then a wait "
-                      "for that step's completion and a host read of its result, one step queued ahead",
-               "transfer": f"page-locked host buffers read and written in place by the kernels over the host link; "
-                           f"{ring_h} input/output buffer pairs in rotation ({ring_h * per_step >> 20} MiB > 2x L2)"}
+               "api": "fnt_batch_create(host_buffers=1) and fnt_batch_set_input_copy(1) once per buffer; per step "
+                      "fnt_batch_launch, then a wait for that step's completion and a host read of its result, one "
+                      "step queued ahead",
+               "transfer": f"input copied host -> device by DMA on the batch's stream, started at launch (overlapping "
+                           f"the previous step); output written in place over the host link; {ring_h} input/output "
+                           f"buffer pairs in rotation ({ring_h * per_step >> 20} MiB > 2x L2)",
+               "in_place_reads": {"value": aggregate(n * steps_e2e, world, el_inplace),
+                                  "ms_per_step": el_inplace / steps_e2e * 1e3,
+                                  "transfer": "kernels read the input across the host link"}}
         st_e2e.copy_(torch.from_numpy(state_snap))
         rb[0].launch(stream)
         stream.synchronize()

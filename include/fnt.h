@@ -257,6 +257,19 @@ FNT_API fnt_status fnt_batch_create(const fnt_plan *plan, const fnt_frame_batch 
  * overlap on the device (they share its intermediate buffers). */
 FNT_API fnt_status fnt_batch_launch(fnt_batch *b, void *stream);
 
+/* Host-buffer batches (host_buffers = 1): with on = 1, every launch first
+ * copies each frame's page-locked input into device memory of the batch's own,
+ * by DMA on a stream of the batch's own, and the kernels read that copy instead
+ * of reading the input across the host link (outputs are still written in
+ * place).  The copy does not wait for `stream`: it starts when
+ * fnt_batch_launch is called, as soon as this batch's previous launch has
+ * consumed its inputs, so it overlaps work queued before it (the previous step
+ * of a stream, say).  The input must therefore hold the frame's data when
+ * fnt_batch_launch is called, not only once the stream reaches the launch.
+ * One copy per frame and launch.  on = 0 returns to the in-place reads.  Waits
+ * for the device to be idle; FNT_ERR_INVALID for a batch without host inputs. */
+FNT_API fnt_status fnt_batch_set_input_copy(fnt_batch *b, int32_t on);
+
 /* Enqueues one stage of the prepared work: stage 0 = the CDC kernel, stage 1 =
  * the AEQ kernel (a stage the op does not have enqueues nothing).  Running
  * stage 0 then stage 1 on one stream equals fnt_batch_launch without a graph;

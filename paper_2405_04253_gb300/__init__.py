@@ -86,6 +86,7 @@ SIGNATURES = {
     "fnt_batch_create": (_I32, [_VP, ctypes.POINTER(BatchC), _I32, _I32, ctypes.POINTER(_VP)]),
     "fnt_batch_launch": (_I32, [_VP, _VP]),
     "fnt_batch_launch_stage": (_I32, [_VP, _I32, _VP]),
+    "fnt_batch_set_input_copy": (_I32, [_VP, _I32]),
     "fnt_batch_kernel_count": (_I32, [_VP]),
     "fnt_batch_destroy": (_I32, [_VP]),
     "fnt_cdc_aeq_run_noalloc": (_I32, [_VP, ctypes.POINTER(FrameC), _VP]),
@@ -258,6 +259,12 @@ class Batch:
 
     def launch(self, stream=None):
         check(lib().fnt_batch_launch(self.handle, _stream_handle(stream)))
+
+    def set_input_copy(self, on: bool):
+        """Host-buffer batches: copy the inputs to the device by DMA on the
+        batch's own stream, started at launch() without waiting for `stream`
+        (the input must hold its data when launch() is called)."""
+        check(lib().fnt_batch_set_input_copy(self.handle, int(bool(on))))
 
     def launch_stage(self, stage: int, stream=None):
         check(lib().fnt_batch_launch_stage(self.handle, stage, _stream_handle(stream)))

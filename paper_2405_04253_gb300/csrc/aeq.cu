@@ -132,30 +132,28 @@ struct SplitInput {
 //   JoinDiff, n' in [0, K): only the difference is kept; lane 0 forms it for
 //     n' = j and lane 1 for n' = j + K/2 (j < K/2), one exchange serving both.
 // Every lane thus produces (N - K)/2 outputs and no discarded one.  Each
-// output v (|true value| <= 32512) is stored as v * wgt, decoded first when
-// the inputs were summed in Z_F.
-template <bool FS>
-__device__ __forceinline__ int32_t join_value(int32_t v, bool fsum) {
+// output v (|true value| <= 32512) is stored as v * wgt, decoded first (DEC)
+// when the inputs were summed in Z_F.
+template <bool DEC>
+__device__ __forceinline__ int32_t join_value(int32_t v) {
     v = rhoc(v);
-    return FS && fsum ? decode(v) : v;
+    return DEC ? decode(v) : v;
 }
 
-template <int NA, int64_t AINV, bool FS, int J>
+template <int NA, int64_t AINV, bool DEC, int J>
 struct JoinBoth {
-    static __device__ __forceinline__ void run(const int32_t (&x)[NA / 2], int32_t *row, int32_t wgt, bool odd,
-                                               bool fsum) {
+    static __device__ __forceinline__ void run(const int32_t (&x)[NA / 2], int32_t *row, int32_t wgt, bool odd) {
         constexpr int32_t W = TwTab<NA, AINV>::tab.w[J];
         const int32_t t = odd ? mulb<18, W>(x[J]) : x[J];         // lane 1 sends alpha^-n' E1[n']
         const int32_t r = __shfl_xor_sync(0xffffffffu, t, 1);
-        row[J] = join_value<FS>(odd ? r - t : t + r, fsum) * wgt;
-        if constexpr (J + 1 < NA / 2) JoinBoth<NA, AINV, FS, J + 1>::run(x, row, wgt, odd, fsum);
+        row[J] = join_value<DEC>(odd ? r - t : t + r) * wgt;
+        if constexpr (J + 1 < NA / 2) JoinBoth<NA, AINV, DEC, J + 1>::run(x, row, wgt, odd);
     }
 };
 
-template <int NA, int64_t AINV, bool FS, int J>
+template <int NA, int64_t AINV, bool DEC, int J>
 struct JoinDiff {
-    static __device__ __forceinline__ void run(const int32_t (&x)[NA / 2], int32_t *row, int32_t wgt, bool odd,
-                                               bool fsum) {
+    static __device__ __forceinline__ void run(const int32_t (&x)[NA / 2], int32_t *row, int32_t wgt, bool odd) {
         constexpr int H = kAeqK / 2;
         constexpr int32_t WA = TwTab<NA, AINV>::tab.w[J], WB = TwTab<NA, AINV>::tab.w[J + H];
         // lane 0 sends E0[j + H] and keeps E0[j]; lane 1 sends alpha^-j E1[j] and
@@ -163,8 +161,8 @@ struct JoinDiff {
         const int32_t send = odd ? mulb<18, WA>(x[J]) : x[J + H];
         const int32_t own = odd ? mulb<18, WB>(x[J + H]) : x[J];
         const int32_t r = __shfl_xor_sync(0xffffffffu, send, 1);
-        row[J] = join_value<FS>(odd ? r - own : own - r, fsum) * wgt;
-        if constexpr (J + 1 < H) JoinDiff<NA, AINV, FS, J + 1>::run(x, row, wgt, odd, fsum);
+        row[J] = join_value<DEC>(odd ? r - own : own - r) * wgt;
+        if constexpr (J + 1 < H) JoinDiff<NA, AINV, DEC, J + 1>::run(x, row, wgt, odd);
     }
 };
 
@@ -293,10 +291,6 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
     const int s1 = (task >> 1) & 3;
     const int g = task & 1;                   // 0: hi group (weight 128), 1: lo group
     const int k0 = 8 * g + 4 * h;             // this lane's 4 gradient taps
-    // tap group of a master tap T (W = T >> 16): hi W >> 7 = T >> 23 (arithmetic
-    // shifts compose), lo W & 127 = (T >> 16) & 127
-    const int tsh = g ? 16 : 23;
-    const int32_t tmask = g ? 127 : -1;
     const bool odd = h != 0;
     const int64_t A2 = (int64_t)prm.rde_a * prm.rde_a;
     const int mu = prm.mu_shift;
@@ -372,6 +366,10 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
             int32_t y[M];
             if (!PER || in_period == 0) {
                 int32_t wv[K];
+                // tap group of a master tap T (W = T >> 16): hi W >> 7 = T >> 23
+                // (arithmetic shifts compose), lo W & 127 = (T >> 16) & 127
+                const int tsh = g ? 16 : 23;
+                const int32_t tmask = g ? 127 : -1;
 #pragma unroll
                 for (int k = 0; k < K; ++k) wv[k] = (T[k] >> tsh) & tmask;
                 if (FS && prm.freq_sum == 2) {
@@ -415,11 +413,18 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
             {
                 // kept outputs n >= K -> block position i = n - K of this task's row;
                 // with summation only the first input lane contributes
-                const int32_t wgt = FS && fsum && s1 != 0 ? 0 : (g ? 1 : 128);
                 int32_t *rrow = red + task * C::RED_ROW;
-                if constexpr (M > K)
-                    JoinBoth<NA, C::AINV, FS, K>::run(y, rrow - K + (odd ? M : 0), wgt, odd, fsum);
-                JoinDiff<NA, C::AINV, FS, 0>::run(y, rrow + (M - K) + (odd ? K / 2 : 0), wgt, odd, fsum);
+                if (FS && fsum) {
+                    // a summed output may exceed the per-pair bound (and wraps with
+                    // freq_sum = 1): the exact signed decode of the residue
+                    const int32_t wgt = s1 != 0 ? 0 : (g ? 1 : 128);
+                    if constexpr (M > K) JoinBoth<NA, C::AINV, true, K>::run(y, rrow - K + (odd ? M : 0), wgt, odd);
+                    JoinDiff<NA, C::AINV, true, 0>::run(y, rrow + (M - K) + (odd ? K / 2 : 0), wgt, odd);
+                } else {
+                    const int32_t wgt = g ? 1 : 128;
+                    if constexpr (M > K) JoinBoth<NA, C::AINV, false, K>::run(y, rrow - K + (odd ? M : 0), wgt, odd);
+                    JoinDiff<NA, C::AINV, false, 0>::run(y, rrow + (M - K) + (odd ? K / 2 : 0), wgt, odd);
+                }
             }
             __syncwarp();
 

@@ -757,11 +757,40 @@ struct fnt_batch {
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaStream_t> side;   // one per pipelined chunk
     std::vector<cudaEvent_t> ev;      // fork (k) and join (C + k) events
+    // Page-locked host inputs (host-buffer batches) and, with the input copy
+    // on, their device copies: frame, host pointer, its device mapping, offset
+    // in dev_in and size.
+    struct Input {
+        int frame;
+        const void *src;
+        const void *view;
+        size_t off, bytes;
+    };
+    std::vector<Input> inputs;
+    bool in_copy = false;
+    char *dev_in = nullptr;
+    cudaStream_t copy = nullptr;      // the batch's own copy stream
+    cudaEvent_t copy_done = nullptr;  // this launch's inputs are on the device
+    cudaEvent_t in_free = nullptr;    // the previous launch has consumed them
 };
 
 static fnt_status batch_enqueue(fnt_batch *bt, cudaStream_t stream) {
     if (bt->side.empty()) return launch_work(bt->plan, bt->work, bt->dev, stream);
     return launch_pipelined(bt->plan, bt->work, bt->dev, stream, bt->side, bt->ev);
+}
+
+// Input copy: the frames' inputs go to the device on the batch's copy stream,
+// which waits only for the batch's previous launch to have consumed them, not
+// for `stream`; `stream` then waits for the copies.
+static fnt_status start_input_copy(fnt_batch *bt, cudaStream_t stream) {
+    cudaError_t e = cudaStreamWaitEvent(bt->copy, bt->in_free, 0);
+    for (size_t k = 0; k < bt->inputs.size() && e == cudaSuccess; ++k) {
+        const fnt_batch::Input &in = bt->inputs[k];
+        e = cudaMemcpyAsync(bt->dev_in + in.off, in.src, in.bytes, cudaMemcpyHostToDevice, bt->copy);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(bt->copy_done, bt->copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, bt->copy_done, 0);
+    return e == cudaSuccess ? FNT_OK : cuda_fail(e, "batch input copy");
 }
 
 extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch *b, int32_t op, int32_t use_graph,
@@ -794,6 +823,7 @@ extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch 
             df.in = (const int8_t *)vin;
             if (op == FNT_OP_AEQ) df.aeq_in = (int8_t *)vin;
             df.out = vout;
+            bt->inputs.push_back({i, b->frames[i].in, vin, 0, in_bytes(b->frames[i], op)});
         }
     }
     layout(bt->work);
@@ -827,9 +857,56 @@ extern "C" fnt_status fnt_batch_create(const fnt_plan *p, const fnt_frame_batch 
     return FNT_OK;
 }
 
+extern "C" fnt_status fnt_batch_set_input_copy(fnt_batch *bt, int32_t on) {
+    if (!bt) return fail(FNT_ERR_INVALID, "null batch");
+    if (on && bt->inputs.empty()) return fail(FNT_ERR_INVALID, "input copy: not a host-buffer batch with input");
+    if ((on != 0) == bt->in_copy) return FNT_OK;
+    cudaError_t e = cudaDeviceSynchronize();          // no launch of the batch is in flight
+    if (e == cudaSuccess && on && !bt->dev_in) {
+        size_t total = 0;
+        for (fnt_batch::Input &in : bt->inputs) {
+            in.off = total;
+            total += (in.bytes + 255) / 256 * 256;
+        }
+        e = cudaMalloc((void **)&bt->dev_in, total);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->copy, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->copy_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->in_free, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(FNT_ERR_NOMEM, "input copy: device memory")
+                                                                    : cuda_fail(e, "input copy setup");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "input copy");
+    // the kernels read the frame table from device memory: repoint the inputs
+    // there (a captured graph stays valid)
+    for (const fnt_batch::Input &in : bt->inputs) {
+        DevFrame &df = bt->work.frames[in.frame];
+        const int8_t *p = on ? (const int8_t *)(bt->dev_in + in.off) : (const int8_t *)in.view;
+        df.in = p;
+        if (bt->work.op == FNT_OP_AEQ) df.aeq_in = (int8_t *)p;
+    }
+    e = cudaMemcpy(bt->dev + bt->work.off_frames, bt->work.frames.data(), bt->work.frames.size() * sizeof(DevFrame),
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "input copy: frame table");
+    bt->in_copy = on != 0;
+    return FNT_OK;
+}
+
+static fnt_status batch_launch_all(fnt_batch *bt, cudaStream_t stream);
+
 extern "C" fnt_status fnt_batch_launch(fnt_batch *bt, void *stream_) {
     if (!bt) return fail(FNT_ERR_INVALID, "null batch");
     cudaStream_t stream = (cudaStream_t)stream_;
+    if (!bt->in_copy) return batch_launch_all(bt, stream);
+    fnt_status st = start_input_copy(bt, stream);
+    if (st == FNT_OK) st = batch_launch_all(bt, stream);
+    if (st == FNT_OK) {
+        cudaError_t e = cudaEventRecord(bt->in_free, stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "batch input release");
+    }
+    return st;
+}
+
+static fnt_status batch_launch_all(fnt_batch *bt, cudaStream_t stream) {
     if (!bt->use_graph) return batch_enqueue(bt, stream);
     if (!bt->exec) {
         cudaStream_t cap;
@@ -858,10 +935,19 @@ extern "C" fnt_status fnt_batch_launch(fnt_batch *bt, void *stream_) {
     return FNT_OK;
 }
 
-extern "C" fnt_status fnt_batch_launch_stage(fnt_batch *bt, int32_t stage, void *stream) {
+extern "C" fnt_status fnt_batch_launch_stage(fnt_batch *bt, int32_t stage, void *stream_) {
     if (!bt) return fail(FNT_ERR_INVALID, "null batch");
     if (stage != 0 && stage != 1) return fail(FNT_ERR_INVALID, "stage must be 0 (CDC) or 1 (AEQ)");
-    return launch_work(bt->plan, bt->work, bt->dev, (cudaStream_t)stream, 1 << stage);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    // with the input copy on, the stage that reads the inputs copies them first
+    const bool reads_input = bt->in_copy && stage == (bt->work.op == FNT_OP_AEQ ? 1 : 0);
+    fnt_status st = reads_input ? start_input_copy(bt, stream) : FNT_OK;
+    if (st == FNT_OK) st = launch_work(bt->plan, bt->work, bt->dev, stream, 1 << stage);
+    if (st == FNT_OK && reads_input) {
+        cudaError_t e = cudaEventRecord(bt->in_free, stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "batch input release");
+    }
+    return st;
 }
 
 extern "C" int32_t fnt_batch_kernel_count(const fnt_batch *bt) { return bt ? work_kernel_count(bt->work) : 0; }
@@ -872,6 +958,10 @@ extern "C" fnt_status fnt_batch_destroy(fnt_batch *bt) {
     if (bt->exec) cudaGraphExecDestroy(bt->exec);
     for (auto &sd : bt->side) cudaStreamDestroy(sd);
     for (auto &e : bt->ev) cudaEventDestroy(e);
+    if (bt->copy) cudaStreamDestroy(bt->copy);
+    if (bt->copy_done) cudaEventDestroy(bt->copy_done);
+    if (bt->in_free) cudaEventDestroy(bt->in_free);
+    cudaFree(bt->dev_in);
     cudaFree(bt->dev);
     delete bt;
     return FNT_OK;

@@ -425,6 +425,63 @@ def test_prepared_batch_on_page_locked_host_buffers(orc):
     assert e.value.status == F.FNT_ERR_INVALID
 
 
+@pytest.mark.parametrize("graph", [True, False])
+def test_prepared_host_batch_input_copy(orc, graph):
+    """Host-buffer batches with the input copied by DMA ahead of the kernels:
+    new data written into the page-locked inputs between launches, two batches
+    queued back to back on one stream (the second's copy not waiting for the
+    first's kernels), per-stage launches, and switching the copy off again all
+    equal the oracle, step by step on a carried state."""
+    f = synth.config2(1 << 13)
+    rng = np.random.default_rng(41)
+    plan = F.Plan(n_aeq=64, alpha_aeq=4080, mu_shift=9, aeq_segment=864, aeq_warmup=0)
+    prm = orc.ChainParams(n_aeq=64, alpha_aeq=4080, mu_shift=9, seg_len=864, warmup=0)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    xs = [f.x, rng.integers(-16, 16, f.x.shape).astype(np.int8)]
+    xh = [torch.from_numpy(x.copy()).pin_memory() for x in xs]
+    oh = [torch.full((nsym, 4), 0x2222, dtype=torch.int16).pin_memory() for _ in xs]
+    T = orc.aeq_init_taps(16, 2048)
+    st = dev(T)
+    bs = [F.Batch(plan, [F.Frame(xh[r], oh[r], f.taps, st)], F.OP_CHAIN, use_graph=graph, host=True) for r in (0, 1)]
+    for b in bs:
+        b.set_input_copy(True)
+    s = torch.cuda.Stream()
+    for step in range(3):
+        new = [rng.integers(-16, 16, f.x.shape).astype(np.int8) for _ in xs] if step else xs
+        for r in (0, 1):
+            xh[r].copy_(torch.from_numpy(new[r]))
+        bs[0].launch(s)
+        bs[1].launch(s)                       # its copy may run during the first batch's kernels
+        s.synchronize()
+        for r in (0, 1):
+            ref, T = orc.chain(new[r], f.taps, prm, T0=T)
+            assert np.array_equal(oh[r].numpy(), ref), (step, r)
+        assert np.array_equal(st.cpu().numpy(), T), step
+    # per-stage launches copy before the CDC stage
+    x3 = rng.integers(-16, 16, f.x.shape).astype(np.int8)
+    xh[0].copy_(torch.from_numpy(x3))
+    bs[0].launch_stage(0, s)
+    bs[0].launch_stage(1, s)
+    s.synchronize()
+    ref, T = orc.chain(x3, f.taps, prm, T0=T)
+    assert np.array_equal(oh[0].numpy(), ref)
+    # and off again: in-place reads of the host input
+    bs[1].set_input_copy(False)
+    x4 = rng.integers(-16, 16, f.x.shape).astype(np.int8)
+    xh[1].copy_(torch.from_numpy(x4))
+    bs[1].launch(s)
+    s.synchronize()
+    ref, T = orc.chain(x4, f.taps, prm, T0=T)
+    assert np.array_equal(oh[1].numpy(), ref)
+    for b in bs:
+        b.close()
+    bd = F.Batch(plan, [F.Frame(dev(f.x), i16((nsym, 4)), f.taps, dev(T))], F.OP_CHAIN)
+    with pytest.raises(F.FntError) as e:
+        bd.set_input_copy(True)                # device buffers: nothing to copy
+    assert e.value.status == F.FNT_ERR_INVALID
+    bd.close()
+
+
 def test_chain_full_size_cfg2_sampled_segments(orc):
     """The benchmark's workload at full size (2^21 samples per polarisation,
     segments of 864 with stream history, carried state), launched as bench.py

@@ -338,3 +338,38 @@ def test_session_submit_many_stops_at_cap_and_bad_request():
     assert e.value.status == F.FNT_ERR_INVALID and s.pending() == 0
     assert s.submit_many(reqs, start=3) == []
     s.close()
+
+
+@pytest.mark.parametrize("variant", ["tensor_gradient", "period3", "segmented_tensor_n64", "cdc_both_items"])
+def test_session_plan_variants_match_sequential_oracle(orc, variant):
+    """The session runs whatever the plan selects (gradient on the tensor cores,
+    an update period, N = 64 segments, two-polarisation CDC items): each link's
+    frames, chained on the device, equal sequential oracle processing."""
+    rng = np.random.default_rng(31)
+    links = make_links(rng, 3)
+    frames = make_frames(rng, 3, 4, lo=2000, hi=9000)
+    kw, okw = {}, {}
+    if variant == "period3":
+        kw, okw = dict(aeq_update_period=3), dict(period=3)
+    elif variant == "segmented_tensor_n64":
+        kw = dict(n_aeq=64, alpha_aeq=4080, aeq_segment=432, aeq_warmup=0)
+        okw = dict(n_aeq=64, alpha_aeq=4080, seg_len=432, warmup=0)
+    plan = F.Plan(mu_shift=MU, **kw)
+    if "tensor" in variant:
+        plan.set_tensor_gradient(True)
+    if variant == "cdc_both_items":
+        plan.set_cdc_items(2)
+    s = F.Session(plan, len(links), 1 << 30, 2)
+    for l, taps in enumerate(links):
+        s.set_link(l, taps)
+    xs, outs = _device_frames(frames, links)
+    assert len(s.submit_many(F.Requests([l for l, _ in frames], xs, outs))) == len(frames)
+    assert all(c[2] == F.FNT_OK for c in _drain(s, len(frames)))
+    prm = orc.ChainParams(mu_shift=MU, **okw)
+    T = {l: orc.aeq_init_taps(16, prm.w0) for l in range(len(links))}
+    for i, (link, x) in enumerate(frames):
+        ref, T[link] = orc.chain(x, links[link], prm, T0=T[link])
+        assert np.array_equal(outs[i].cpu().numpy(), ref), (variant, i)
+    for l in range(len(links)):
+        assert np.array_equal(s.get_link_state(l), T[l])
+    s.close()

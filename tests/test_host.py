@@ -45,6 +45,55 @@ def test_binding_covers_every_declared_symbol():
     assert sorted(fnt.SIGNATURES) == header_functions()
 
 
+def _c_layout(struct: str, fields) -> dict:
+    """sizeof and offsetof of a struct of include/fnt.h, compiled by the host C
+    compiler from the header alone."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "fnt.h"', "int main(void) {",
+           f'  printf("size %zu\\n", sizeof({struct}));']
+    src += [f'  printf("{f} %zu\\n", offsetof({struct}, {f}));' for f in fields]
+    src += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        with open(c, "w") as fh:
+            fh.write("\n".join(src) + "\n")
+        subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
+
+
+def test_binding_struct_layouts_match_the_header():
+    """Every struct the binding passes through the C ABI has the header's size
+    and field offsets (ctypes structures and the numpy record types)."""
+    import paper_2405_04253_gb300 as fnt
+    ctypes_structs = {
+        "fnt_plan_desc": (fnt.PlanDesc, None),
+        "fnt_frame": (fnt.FrameC, {"in_": "in"}),
+        "fnt_frame_batch": (fnt.BatchC, None),
+        "fnt_op_counts": (fnt.OpCounts, None),
+        "fnt_completion": (fnt.Completion, None),
+    }
+    for struct, (cls, rename) in ctypes_structs.items():
+        names = [f[0] for f in cls._fields_]
+        cnames = [(rename or {}).get(n, n) for n in names]
+        lay = _c_layout(struct, cnames)
+        assert lay["size"] == ctypes.sizeof(cls), struct
+        for n, cn in zip(names, cnames):
+            assert lay[cn] == getattr(cls, n).offset, (struct, n)
+    for struct, dt, rename in (("fnt_request", fnt.REQUEST_DTYPE, {"in_": "in"}),
+                               ("fnt_completion", fnt.COMPLETION_DTYPE, {})):
+        cnames = [rename.get(n, n) for n in dt.names]
+        lay = _c_layout(struct, cnames)
+        assert lay["size"] == dt.itemsize, struct
+        for n, cn in zip(dt.names, cnames):
+            assert lay[cn] == dt.fields[n][1], (struct, n)
+
+
 def test_library_is_sm103a_only():
     import importlib
     b = importlib.import_module("paper_2405_04253_gb300.build")
