@@ -475,6 +475,16 @@ def cpu_baseline(x_np, taps, wl, out_dev=None, n_seg=96, procs=None, T0=None):
     if out_dev is not None:
         got = out_dev.cpu().numpy()
         cb["sample_bitexact"] = bool(all(np.array_equal(got[k:k + o.shape[0]], o) for (k, o) in res.values()))
+    # the same oracle on one core, over segments spread through the stream
+    n1 = min(24, len(segs))
+    one = [segs[(i * len(segs)) // n1] for i in range(n1)]
+    pool1 = OraclePool(x_np, taps, _prm_kw(wl), 1, init_taps() if T0 is None else T0)
+    try:
+        secs1, samples1, _ = pool1.run(one)
+    finally:
+        pool1.close()
+    cb["single_core"] = {"value": round(samples1 / secs1 / 1e9, 7), "cores": 1, "seconds": round(secs1, 2),
+                         "sample": f"{n1} of {total} AEQ segments spread over the stream ({samples1} output samples)"}
     return cb
 
 
