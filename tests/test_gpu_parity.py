@@ -482,6 +482,35 @@ def test_prepared_host_batch_input_copy(orc, graph):
     bd.close()
 
 
+def test_prepared_aeq_batch_input_copy(orc):
+    """An AEQ-only host-buffer batch with the input copy: the AEQ stage is the
+    one that reads the input, by graph launch and by per-stage launch, on a
+    carried state."""
+    rng = np.random.default_rng(42)
+    plan = F.Plan(mu_shift=9)
+    n = 3000
+    xh = torch.from_numpy(rng.integers(-16, 16, (n, 4)).astype(np.int8)).pin_memory()
+    oh = torch.zeros((n, 4), dtype=torch.int16).pin_memory()
+    T = orc.aeq_init_taps(16, 2048)
+    st = dev(T)
+    b = F.Batch(plan, [F.Frame(xh, oh, None, st)], F.OP_AEQ, use_graph=True, host=True)
+    b.set_input_copy(True)
+    s = torch.cuda.Stream()
+    for step in range(3):
+        x = rng.integers(-16, 16, (n, 4)).astype(np.int8)
+        xh.copy_(torch.from_numpy(x))
+        if step < 2:
+            b.launch(s)
+        else:
+            b.launch_stage(0, s)              # nothing: the op has no CDC stage
+            b.launch_stage(1, s)
+        s.synchronize()
+        ref, T = orc.aeq(x, T, 32, 2, mu_shift=9, rde_a=64)
+        assert np.array_equal(oh.numpy(), ref), step
+        assert np.array_equal(st.cpu().numpy(), T), step
+    b.close()
+
+
 def test_chain_full_size_cfg2_sampled_segments(orc):
     """The benchmark's workload at full size (2^21 samples per polarisation,
     segments of 864 with stream history, carried state), launched as bench.py

@@ -373,3 +373,35 @@ def test_session_plan_variants_match_sequential_oracle(orc, variant):
     for l in range(len(links)):
         assert np.array_equal(s.get_link_state(l), T[l])
     s.close()
+
+
+def test_session_tiny_and_empty_frames_in_a_burst(orc):
+    """Zero-length, one-sample and short frames mixed with normal ones in one
+    admitted burst, several per link: every completion is OK, every output and
+    every link's final taps equal sequential oracle processing."""
+    rng = np.random.default_rng(32)
+    links = make_links(rng, 3)
+    sizes = [0, 1, 2, 3, 17, 33, 4000, 0, 1, 5000, 2, 64, 0]
+    frames = [(i % 3, rng.integers(-16, 16, (n, 2, 2)).astype(np.int8)) for i, n in enumerate(sizes)]
+    ref, Tref = oracle_sequential(orc, links, frames)
+    s = F.Session(F.Plan(mu_shift=MU), len(links), 1 << 28, 2)
+    for l, taps in enumerate(links):
+        s.set_link(l, taps)
+    xs, outs = [], []
+    for link, x in frames:
+        nsym = F.chain_nsym(x.shape[0], links[link].shape[0])
+        xs.append(torch.from_numpy(x).cuda() if x.shape[0] else torch.zeros((0, 2, 2), dtype=torch.int8, device="cuda"))
+        outs.append(torch.full((max(nsym, 1), 4), 0x1111, dtype=torch.int16, device="cuda"))
+    torch.cuda.synchronize()
+    tk = s.submit_many(F.Requests([l for l, _ in frames], xs, outs))
+    assert len(tk) == len(frames)
+    done = _drain(s, len(frames))
+    assert all(c[2] == F.FNT_OK for c in done)
+    nsyms = {c[0]: c[3] for c in done}
+    for i, (link, x) in enumerate(frames):
+        nsym = ref[i].shape[0]
+        assert nsyms[tk[i]] == nsym, i
+        assert np.array_equal(outs[i].cpu().numpy()[:nsym], ref[i]), i
+    for l in range(len(links)):
+        assert np.array_equal(s.get_link_state(l), Tref[l])
+    s.close()
