@@ -318,6 +318,17 @@ def run_fnt(args, rank, world, local_rank):
     for k in range(k2):
         step_staged(k, evs2[k])
     torch.cuda.synchronize()
+    # ten more timed blocks of graph steps: best and median per step, beside the
+    # K-step figure that `value` reports
+    rep_steps = max(1, args.steps // 10)
+    evr = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(10)]
+    for j in range(10):
+        evr[j][0].record(stream)
+        for k in range(rep_steps):
+            step(k)
+        evr[j][1].record(stream)
+    torch.cuda.synchronize()
+    rep_ms = sorted(e[0].elapsed_time(e[1]) / rep_steps for e in evr)
     clk = clocks.stop()
     cdc_ms = [e[0].elapsed_time(e[1]) for e in evs2]
     aeq_ms = [e[1].elapsed_time(e[2]) for e in evs2]
@@ -440,6 +451,10 @@ def run_fnt(args, rank, world, local_rank):
                        "note": f"per-kernel times from {k2} extra steps run as separate launches with events "
                                f"between them; the timed steps replay the same launches as one graph per ring slot, "
                                f"back to back, timed by one event pair"},
+        "repeat": {"blocks": 10, "steps_per_block": rep_steps, "best_ms_per_step": round(rep_ms[0], 4),
+                   "median_ms_per_step": round(statistics.median(rep_ms), 4),
+                   "best_value": round(aggregate(n, world, rep_ms[0] * 1e-3), 4),
+                   "median_value": round(aggregate(n, world, statistics.median(rep_ms) * 1e-3), 4)},
         "hbm": {"achieved_gbs": round(hbm_bytes / (ms_per_step * 1e-3) / 1e9, 2), "peak_gbs": 6795.1,
                 "frac": round(hbm_bytes / (ms_per_step * 1e-3) / 1e9 / 6795.1, 5),
                 "bytes_per_step": hbm_bytes, "note": "algorithmic: int8 input + int16 output"},
@@ -475,8 +490,9 @@ def cpu_baseline(x_np, taps, wl, out_dev=None, n_seg=96, procs=None, T0=None):
     if out_dev is not None:
         got = out_dev.cpu().numpy()
         cb["sample_bitexact"] = bool(all(np.array_equal(got[k:k + o.shape[0]], o) for (k, o) in res.values()))
-    # the same oracle on one core, over segments spread through the stream
-    n1 = min(24, len(segs))
+    # the same oracle on one core, over segments spread through the stream (about
+    # 20k symbols: two seconds or so)
+    n1 = max(1, min(24, len(segs), 20736 // max(1, int(wl["segment"]) + int(wl["warmup"]))))
     one = [segs[(i * len(segs)) // n1] for i in range(n1)]
     pool1 = OraclePool(x_np, taps, _prm_kw(wl), 1, init_taps() if T0 is None else T0)
     try:
@@ -548,11 +564,13 @@ def run_cfg1(args):
         b.launch(stream)
         evs[k][1].record(stream)
     torch.cuda.synchronize()
-    ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    per = sorted(e[0].elapsed_time(e[1]) for e in evs)
+    ms = statistics.mean(per)
     ops = cdc_ops(n, 48, n_pol=1)
     return {"workload": "cfg1: single-pol FNT-CDC, 65,536 samples, 17 taps, N=64 alpha=4080 S=48",
             "metric": "Msamples/s", "value": round(n / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
             "steps": args.steps, "gpu_launches_per_step": b.kernel_count(),
+            "repeat": {"launches": len(per), "best_ms": round(per[0], 4), "median_ms": round(statistics.median(per), 4)},
             "roofline": {"bound": "alu", "kernel": "cdc_kernel<cdc>", "achieved": round(ops / (ms * 1e-3) / 1e12, 3),
                          "peak": round(alu_peak_ops() / 1e12, 2), "unit": "Tops/s (int32, algorithmic)",
                          "frac": round(ops / (ms * 1e-3) / alu_peak_ops(), 4)},
@@ -590,6 +608,14 @@ def run_cfg3(args):
     ev[1].record(stream)
     torch.cuda.synchronize()
     ms_batched = ev[0].elapsed_time(ev[1]) / reps
+    # ten more batched launches, each timed alone: best and median
+    evr = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(10)]
+    for e in evr:
+        e[0].record(stream)
+        batch.launch(stream)
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    rep_ms = sorted(e[0].elapsed_time(e[1]) for e in evr)
     # one launch pair per frame (prepared per-frame batches, no per-call setup)
     singles = [fnt.Batch(plan, [fr], fnt.OP_CHAIN, use_graph=False) for fr in frames]
     for fr in frames:
@@ -617,6 +643,8 @@ def run_cfg3(args):
     return {"workload": f"cfg3: {len(frames)} PDM frames, lengths log-uniform 2^12..2^18 samples "
                         f"({total} samples), 10-80 km (5-19 taps), FNT-AEQ N=32 alpha=2, fresh taps per frame",
             "metric": "Gsamples/s", "batched": round(total / (ms_batched * 1e-3) / 1e9, 3),
+            "repeat": {"launches": 10, "best_ms": round(rep_ms[0], 3), "median_ms": round(statistics.median(rep_ms), 3),
+                       "best_value": round(total / (rep_ms[0] * 1e-3) / 1e9, 3)},
             "per_frame_launches": round(total / (ms_single * 1e-3) / 1e9, 3),
             "speedup": round(ms_single / ms_batched, 2), "ms_batched": round(ms_batched, 3),
             "ms_per_frame_launches": round(ms_single, 3), "gpu_launches_batched": batch.kernel_count(),
