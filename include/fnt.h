@@ -293,6 +293,12 @@ FNT_API fnt_status fnt_plan_set_launch(fnt_plan *plan, int32_t cdc_warps, int32_
  * piece is a latency-bound set of serial chains.) */
 FNT_API fnt_status fnt_plan_set_pipeline(fnt_plan *plan, int32_t chunks);
 
+/* The plan's initial AEQ taps (the state a frame without aeq_state, or a newly
+ * configured serving link, starts from): HOST int32 [4 (S2)][4 (S1)][16],
+ * zero except the centre tap of the four diagonal filters, tap_init << 16.
+ * Copying it into a frame's aeq_state starts that state's adaptation there. */
+FNT_API fnt_status fnt_plan_initial_taps(const fnt_plan *plan, int32_t *state);
+
 /* CDC work items created after this call cover 32 overlap-save blocks of one
  * polarisation (pols = 1) or of both polarisations of a PDM frame (pols = 2);
  * 0 (default) picks 2 when the work fills the GPU at least twice over and 1

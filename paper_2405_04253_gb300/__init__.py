@@ -79,6 +79,7 @@ SIGNATURES = {
     "fnt_plan_set_pipeline": (_I32, [_VP, _I32]),
     "fnt_plan_set_tensor_gradient": (_I32, [_VP, _I32]),
     "fnt_plan_set_cdc_items": (_I32, [_VP, _I32]),
+    "fnt_plan_initial_taps": (_I32, [_VP, _VP]),
     "fnt_op_counts_for": (_I32, [ctypes.POINTER(PlanDesc), _I32, ctypes.POINTER(OpCounts)]),
     "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
     "fnt_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
@@ -188,6 +189,12 @@ class Plan:
 
     def set_pipeline(self, chunks: int):
         check(lib().fnt_plan_set_pipeline(self.handle, chunks))
+
+    def initial_state(self) -> np.ndarray:
+        """The plan's initial AEQ taps, int32 [4 (S2)][4 (S1)][16]."""
+        st = np.zeros((4, 4, 16), np.int32)
+        check(lib().fnt_plan_initial_taps(self.handle, st.ctypes.data))
+        return st
 
     def set_cdc_items(self, pols: int):
         """CDC items of one (1) or both (2) polarisations; 0 = automatic."""

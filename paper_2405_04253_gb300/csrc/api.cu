@@ -243,6 +243,12 @@ extern "C" fnt_status fnt_plan_set_pipeline(fnt_plan *p, int32_t chunks) {
     return FNT_OK;
 }
 
+extern "C" fnt_status fnt_plan_initial_taps(const fnt_plan *p, int32_t *state) {
+    if (!p || !state) return fail(FNT_ERR_INVALID, "null argument");
+    memcpy(state, p->h_init, sizeof p->h_init);
+    return FNT_OK;
+}
+
 extern "C" fnt_status fnt_plan_set_cdc_items(fnt_plan *p, int32_t pols) {
     if (!p) return fail(FNT_ERR_INVALID, "null plan");
     if (pols < 0 || pols > 2) return fail(FNT_ERR_INVALID, "pols per CDC item must be 0, 1 or 2");

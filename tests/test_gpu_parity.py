@@ -511,6 +511,23 @@ def test_prepared_aeq_batch_input_copy(orc):
     b.close()
 
 
+@pytest.mark.parametrize("tap_init", [2048, 1000])
+def test_plan_initial_taps_equal_the_oracle_init(orc, tap_init):
+    """The plan's initial AEQ taps (fnt_plan_initial_taps) are the oracle's
+    init, and a frame state started from them gives the same bits as a frame
+    without a state."""
+    plan = F.Plan(mu_shift=9, tap_init=tap_init)
+    init = plan.initial_state()
+    assert np.array_equal(init, orc.aeq_init_taps(16, tap_init))
+    rng = np.random.default_rng(43)
+    x = rng.integers(-16, 16, (2000, 4)).astype(np.int8)
+    o1, o2 = i16((2000, 4)), i16((2000, 4))
+    F.aeq_run(plan, [F.Frame(dev(x), o1)])
+    F.aeq_run(plan, [F.Frame(dev(x), o2, None, dev(init))])
+    torch.cuda.synchronize()
+    assert np.array_equal(o1.cpu().numpy(), o2.cpu().numpy())
+
+
 def test_chain_full_size_cfg2_sampled_segments(orc):
     """The benchmark's workload at full size (2^21 samples per polarisation,
     segments of 864 with stream history, carried state), launched as bench.py
