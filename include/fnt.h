@@ -293,6 +293,15 @@ FNT_API fnt_status fnt_plan_set_launch(fnt_plan *plan, int32_t cdc_warps, int32_
  * piece is a latency-bound set of serial chains.) */
 FNT_API fnt_status fnt_plan_set_pipeline(fnt_plan *plan, int32_t chunks);
 
+/* Caps the AEQ warps resident per SM for later launches of this plan
+ * (autotuner hook): each AEQ CTA then reserves enough shared memory that at
+ * most max(1, max_warps_per_sm / aeq warps per CTA) CTAs share an SM.  0
+ * (default) lets resources decide.  Long serial AEQ chains (frames with fresh
+ * taps and no segments) finish sooner when fewer share an SM, which can
+ * shorten a batch whose longest chain sets its time.  Results do not depend on
+ * it.  FNT_ERR_INVALID outside [0, 64]. */
+FNT_API fnt_status fnt_plan_set_aeq_occupancy(fnt_plan *plan, int32_t max_warps_per_sm);
+
 /* The plan's initial AEQ taps (the state a frame without aeq_state, or a newly
  * configured serving link, starts from): HOST int32 [4 (S2)][4 (S1)][16],
  * zero except the centre tap of the four diagonal filters, tap_init << 16.

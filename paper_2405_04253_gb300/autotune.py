@@ -1,8 +1,8 @@
 """Launch-shape autotuner for libfnt.
 
-Times each candidate (CDC warps per CTA, AEQ warps per CTA) on a prepared batch
-with CUDA events around each stage on the launching stream, after warm-up,
-and keeps the fastest per stage.  Results are cached in a JSON file keyed by
+Times each candidate (CDC warps per CTA; AEQ warps per CTA with a cap on the
+AEQ warps resident per SM) on a prepared batch with CUDA events around each
+stage on the launching stream, after warm-up, and keeps the fastest per stage.  Results are cached in a JSON file keyed by
 the workload's shape, so a later run with the same shape reuses them.  Only
 launch shapes change: results are bit-identical for every candidate.
 """
@@ -14,6 +14,7 @@ import os
 from . import OP_CHAIN, Batch, Plan
 
 CANDIDATES = (1, 2, 3, 4)
+OCCUPANCY = (0, 12, 16, 20)          # AEQ warps per SM cap (0: none)
 
 
 def _key(plan: Plan, frames, op: int) -> str:
@@ -38,8 +39,9 @@ def _time_stage(batch: Batch, stage: int, reps: int, stream) -> float:
 
 
 def tune(plan: Plan, frames, op: int = OP_CHAIN, reps: int = 20, cache: str | None = None) -> dict:
-    """Picks and applies the fastest warps-per-CTA for each stage of `op` on
-    these frames; returns {"cdc_warps", "aeq_warps", "cdc_ms", "aeq_ms"}."""
+    """Picks and applies the fastest launch shape for each stage of `op` on
+    these frames; returns {"cdc_warps", "aeq_warps", "aeq_occupancy", "cdc_ms",
+    "aeq_ms"}."""
     import torch
     key = _key(plan, frames, op)
     if cache and os.path.exists(cache):
@@ -50,6 +52,7 @@ def tune(plan: Plan, frames, op: int = OP_CHAIN, reps: int = 20, cache: str | No
             hit = None
         if hit:
             plan.set_launch(hit["cdc_warps"], hit["aeq_warps"])
+            plan.set_aeq_occupancy(hit.get("aeq_occupancy", 0))
             return hit
     stream = torch.cuda.current_stream()
     batch = Batch(plan, frames, op, use_graph=False)
@@ -58,17 +61,25 @@ def tune(plan: Plan, frames, op: int = OP_CHAIN, reps: int = 20, cache: str | No
         if stage == 0 and op == 1 or stage == 1 and op == 0:
             continue
         for w in CANDIDATES:
-            if stage == 0:
-                plan.set_launch(cdc_warps=w)
-            else:
-                plan.set_launch(aeq_warps=w)
-            ms = _time_stage(batch, stage, reps, stream)
-            if name + "_ms" not in best or ms < best[name + "_ms"]:
-                best[name + "_ms"] = ms
-                best[name + "_warps"] = w
+            for occ in (OCCUPANCY if stage == 1 else (0,)):
+                if stage == 0:
+                    plan.set_launch(cdc_warps=w)
+                else:
+                    if occ and occ < w:
+                        continue
+                    plan.set_launch(aeq_warps=w)
+                    plan.set_aeq_occupancy(occ)
+                ms = _time_stage(batch, stage, reps, stream)
+                if name + "_ms" not in best or ms < best[name + "_ms"]:
+                    best[name + "_ms"] = ms
+                    best[name + "_warps"] = w
+                    if stage == 1:
+                        best["aeq_occupancy"] = occ
     best.setdefault("cdc_warps", 4)
     best.setdefault("aeq_warps", 2)
+    best.setdefault("aeq_occupancy", 0)
     plan.set_launch(best["cdc_warps"], best["aeq_warps"])
+    plan.set_aeq_occupancy(best["aeq_occupancy"])
     batch.close()
     if cache:
         data = {}

@@ -17,9 +17,11 @@
 // so each lane runs ordinary N/2-point transforms with compile-time twiddles
 // and one shuffle per output finishes the inverse.  The zero-padded taps sit in
 // the first half, so the forward split needs no shuffle at all.
-// Each lane holds the 16 master taps of its filter S1 -> S2 (all four lanes of
-// a filter hold them), accumulates the gradient of 4 of them, and the four
-// lanes swap their updated quarters.  The gradient itself, a (4 inputs x 16
+// At P = 1 the 16 master taps of each filter S1 -> S2 sit in a per-warp table
+// in shared memory: each of the filter's four lanes accumulates the gradient of
+// 4 of them, updates those 4 and writes them back, and every lane reads all 16
+// for its tap transform.  At P > 1 every lane of the filter holds all 16 in
+// registers and the four lanes swap their updated quarters once per period.  The gradient itself, a (4 inputs x 16
 // taps) x symbols x (2 outputs) contraction, runs exactly on the tensor cores
 // (gradient_mma below).  The input spectra (taps-independent) are
 // computed 8 blocks ahead, one full N-point transform per lane, with N^-1
@@ -27,6 +29,8 @@
 // and applied after every P-th block and the last one; in between the taps do
 // not change, so each lane keeps its tap half-spectrum in shared memory and
 // transforms the taps once per period.
+#include <algorithm>
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -63,7 +67,12 @@ struct AeqCfg {
     static constexpr int EZH = 8 * EZ_ROW;                   // e z limbs [o, limb][SA] as f16
     static constexpr int EZ = EZH > 3 * SA ? EZH : 3 * SA;   // ... or z [2][SA] and e [SA] as int32
     static constexpr int WORDS = 2 * XS + XF + RED + EZ;     // xs double-buffered
-    static constexpr int WCACHE = 32 * M;                    // tap half-spectra [M][lane], P > 1 only
+    // then, at P = 1, the master taps [filter (o, s1)][k] (rows padded so that
+    // 16-byte accesses are conflict-free); at P > 1 the tap half-spectra
+    // [M][lane] of the period (the taps then stay in registers)
+    static constexpr int TROW = K + 4;
+    static constexpr int TAPS = 8 * TROW;
+    static constexpr int WCACHE = 32 * M;
     static_assert(SA % 16 == 0 && (2 * XS + XF) % 4 == 0 && RED % 4 == 0 && WORDS % 4 == 0,
                   "16-byte aligned regions");
     static constexpr int32_t NINV = zcent(zinv(NA));
@@ -276,14 +285,15 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     const int period = PER ? prm.period : 1;
-    const int words = C::WORDS + (PER ? C::WCACHE : 0);
+    const int words = C::WORDS + (PER ? C::WCACHE : C::TAPS);
     uint32_t *xs2 = smem + warp * words;          // two staging buffers of C::XS words
     int32_t *xf = (int32_t *)(xs2 + 2 * C::XS);
     int32_t *red = xf + C::XF;
     uint32_t *ezh = (uint32_t *)(red + C::RED);
     int32_t *zs = (int32_t *)ezh;                 // integer gradient: z of both outputs, then e
     int32_t *es = zs + 2 * SA;
-    int32_t *wcache = (int32_t *)(ezh + C::EZ) + lane;   // stride 32: conflict-free
+    int32_t *tsm = (int32_t *)(ezh + C::EZ);             // P = 1: the warp's master taps, [filter][TROW]
+    int32_t *wcache = tsm + lane;                         // P > 1: stride 32, conflict-free
 
     const int h = lane & 1;                   // frequency parity held by this lane
     const int task = lane >> 1;
@@ -291,6 +301,9 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
     const int s1 = (task >> 1) & 3;
     const int g = task & 1;                   // 0: hi group (weight 128), 1: lo group
     const int k0 = 8 * g + 4 * h;             // this lane's 4 gradient taps
+    // the 16 master taps of this lane's filter S1 -> S2 live in the warp's tap
+    // table; the filter's four lanes (g, h) each own and update 4 of them
+    int32_t *trow = tsm + (task >> 1) * C::TROW;
     const bool odd = h != 0;
     const int64_t A2 = (int64_t)prm.rde_a * prm.rde_a;
     const int mu = prm.mu_shift;
@@ -303,9 +316,18 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
         const uint32_t *xin = (const uint32_t *)fr.aeq_in;
         int16_t *out = (int16_t *)fr.out;
 
-        int32_t T[K];
+        // P = 1: this lane's taps k0 .. k0 + 3 (T[0..3]), the filter's 16 in the
+        // table; P > 1: all 16 of the filter in registers
+        int32_t T[PER ? K : 4];
+        if constexpr (PER) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) T[k] = ch.init[(s2 * 4 + s1) * K + k];
+            for (int k = 0; k < K; ++k) T[k] = ch.init[(s2 * 4 + s1) * K + k];
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) T[kk] = ch.init[(s2 * 4 + s1) * K + k0 + kk];
+            __syncwarp();                         // the previous item's last reads of the table
+            *(int4 *)(trow + k0) = make_int4(T[0], T[1], T[2], T[3]);
+        }
 
         const int64_t nblk = (ch.end - ch.begin + SA - 1) / SA;
         int64_t acc[4] = {0, 0, 0, 0};            // gradient of taps k0 .. k0 + 3 over the period
@@ -370,8 +392,19 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                 // (arithmetic shifts compose), lo W & 127 = (T >> 16) & 127
                 const int tsh = g ? 16 : 23;
                 const int32_t tmask = g ? 127 : -1;
+                if constexpr (PER) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) wv[k] = (T[k] >> tsh) & tmask;
+                    for (int k = 0; k < K; ++k) wv[k] = (T[k] >> tsh) & tmask;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < K / 4; ++q) {
+                        const int4 t4 = *(const int4 *)(trow + 4 * q);
+                        wv[4 * q] = (t4.x >> tsh) & tmask;
+                        wv[4 * q + 1] = (t4.y >> tsh) & tmask;
+                        wv[4 * q + 2] = (t4.z >> tsh) & tmask;
+                        wv[4 * q + 3] = (t4.w >> tsh) & tmask;
+                    }
+                }
                 if (FS && prm.freq_sum == 2) {
                     // guard: 16 sum |w| of every (output, group) over the four
                     // inputs within 32767, so every summed output decodes exactly
@@ -503,34 +536,49 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                     int32_t nv[4];
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
-                        const int32_t cur = h ? (g ? T[12 + kk] : T[4 + kk]) : (g ? T[8 + kk] : T[kk]);
+                        // T[k0 + kk], by selects (no dynamic register indexing)
+                        const int32_t cur =
+                            PER ? (h ? (g ? T[(12 + kk) % (PER ? K : 4)] : T[(4 + kk) % (PER ? K : 4)])
+                                     : (g ? T[(8 + kk) % (PER ? K : 4)] : T[kk]))
+                                : T[kk];
                         int64_t v = (int64_t)cur + (acc[kk] >> mu);
                         v = v < -(1ll << 29) ? -(1ll << 29) : (v > (1ll << 29) - 1 ? (1ll << 29) - 1 : v);
                         nv[kk] = (int32_t)v;
                         acc[kk] = 0;
                     }
-                    // gather the filter's 16 taps from its four lanes (lane bit 0 = h, bit 1 = g)
+                    if constexpr (PER) {
+                        // gather the filter's 16 taps from its four lanes (lane bit 0 = h,
+                        // bit 1 = g); once per period
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const int32_t a = nv[kk];                                 // (g, h)
-                        const int32_t b = __shfl_xor_sync(0xffffffffu, a, 1);     // (g, 1-h)
-                        const int32_t c2 = __shfl_xor_sync(0xffffffffu, a, 2);    // (1-g, h)
-                        const int32_t d = __shfl_xor_sync(0xffffffffu, b, 2);     // (1-g, 1-h)
-                        const int32_t q00 = g ? (h ? d : c2) : (h ? b : a);       // g=0, h=0
-                        const int32_t q01 = g ? (h ? c2 : d) : (h ? a : b);       // g=0, h=1
-                        const int32_t q10 = g ? (h ? b : a) : (h ? d : c2);       // g=1, h=0
-                        const int32_t q11 = g ? (h ? a : b) : (h ? c2 : d);       // g=1, h=1
-                        T[kk] = q00;
-                        T[4 + kk] = q01;
-                        T[8 + kk] = q10;
-                        T[12 + kk] = q11;
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const int32_t a = nv[kk];                                 // (g, h)
+                            const int32_t b = __shfl_xor_sync(0xffffffffu, a, 1);     // (g, 1-h)
+                            const int32_t c2 = __shfl_xor_sync(0xffffffffu, a, 2);    // (1-g, h)
+                            const int32_t d = __shfl_xor_sync(0xffffffffu, b, 2);     // (1-g, 1-h)
+                            T[kk] = g ? (h ? d : c2) : (h ? b : a);                   // g=0, h=0
+                            T[4 + kk] = g ? (h ? c2 : d) : (h ? a : b);               // g=0, h=1
+                            T[8 + kk] = g ? (h ? b : a) : (h ? d : c2);               // g=1, h=0
+                            T[12 + kk] = g ? (h ? a : b) : (h ? c2 : d);              // g=1, h=1
+                        }
+                    } else {
+                        // publish this lane's quarter of the filter's taps; the next
+                        // block's tap transform reads all 16 from the table
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) T[kk] = nv[kk];
+                        *(int4 *)(trow + k0) = make_int4(T[0], T[1], T[2], T[3]);
+                        __syncwarp();
                     }
                 }
             }
         }
-        if (ch.write_state && g == 0 && h == 0) {
+        if (ch.write_state) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) fr.state[(s2 * 4 + s1) * K + k] = T[k];
+            for (int kk = 0; kk < 4; ++kk) {
+                const int32_t v = PER ? (h ? (g ? T[(12 + kk) % (PER ? K : 4)] : T[(4 + kk) % (PER ? K : 4)])
+                                           : (g ? T[(8 + kk) % (PER ? K : 4)] : T[kk]))
+                                      : T[kk];
+                fr.state[(s2 * 4 + s1) * K + k0 + kk] = v;
+            }
         }
         __syncwarp();
     }
@@ -543,35 +591,41 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
 int aeq_mults_per_block(int na) { return 32 * na; }
 
 size_t aeq_smem_bytes(int na, int warps, int period) {
-    const int words = na == 64 ? AeqCfg<64, 4080>::WORDS + (period > 1 ? AeqCfg<64, 4080>::WCACHE : 0)
-                               : AeqCfg<32, 2>::WORDS + (period > 1 ? AeqCfg<32, 2>::WCACHE : 0);
+    const int words = na == 64 ? AeqCfg<64, 4080>::WORDS + (period > 1 ? AeqCfg<64, 4080>::WCACHE : AeqCfg<64, 4080>::TAPS)
+                               : AeqCfg<32, 2>::WORDS + (period > 1 ? AeqCfg<32, 2>::WCACHE : AeqCfg<32, 2>::TAPS);
     return (size_t)warps * words * sizeof(uint32_t);
 }
 
 template <int NA, int64_t ALPHA, bool PER, bool MMA, bool FS>
-static cudaError_t aeq_configure_one() {
+static cudaError_t aeq_configure_one(int max_smem) {
+    // up to the device's opt-in maximum: launches may reserve more than they use
+    // to cap the CTAs per SM
     return cudaFuncSetAttribute(aeq_kernel<NA, ALPHA, PER, MMA, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)aeq_smem_bytes(NA, 4, PER ? 2 : 1));
+                                std::max(max_smem, (int)aeq_smem_bytes(NA, 4, PER ? 2 : 1)));
 }
 
 template <int NA, int64_t ALPHA, bool PER, bool MMA>
-static cudaError_t aeq_configure_fs() {
-    cudaError_t e = aeq_configure_one<NA, ALPHA, PER, MMA, false>();
-    return e == cudaSuccess ? aeq_configure_one<NA, ALPHA, PER, MMA, true>() : e;
+static cudaError_t aeq_configure_fs(int max_smem) {
+    cudaError_t e = aeq_configure_one<NA, ALPHA, PER, MMA, false>(max_smem);
+    return e == cudaSuccess ? aeq_configure_one<NA, ALPHA, PER, MMA, true>(max_smem) : e;
 }
 
 template <int NA, int64_t ALPHA>
-static cudaError_t aeq_configure_n() {
-    cudaError_t e = aeq_configure_fs<NA, ALPHA, false, false>();
-    if (e == cudaSuccess) e = aeq_configure_fs<NA, ALPHA, true, false>();
-    if (e == cudaSuccess) e = aeq_configure_fs<NA, ALPHA, false, true>();
-    if (e == cudaSuccess) e = aeq_configure_fs<NA, ALPHA, true, true>();
+static cudaError_t aeq_configure_n(int max_smem) {
+    cudaError_t e = aeq_configure_fs<NA, ALPHA, false, false>(max_smem);
+    if (e == cudaSuccess) e = aeq_configure_fs<NA, ALPHA, true, false>(max_smem);
+    if (e == cudaSuccess) e = aeq_configure_fs<NA, ALPHA, false, true>(max_smem);
+    if (e == cudaSuccess) e = aeq_configure_fs<NA, ALPHA, true, true>(max_smem);
     return e;
 }
 
 cudaError_t aeq_configure() {
-    cudaError_t e = aeq_configure_n<64, 4080>();
-    return e == cudaSuccess ? aeq_configure_n<32, 2>() : e;
+    int dev = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = aeq_configure_n<64, 4080>(max_smem);
+    return e == cudaSuccess ? aeq_configure_n<32, 2>(max_smem) : e;
 }
 
 template <int NA, int64_t ALPHA, bool PER, bool MMA>
@@ -601,10 +655,11 @@ static void aeq_launch_n(dim3 grid, dim3 block, size_t smem, cudaStream_t stream
 }
 
 cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,
-                       int warps, int grid, cudaStream_t stream) {
+                       int warps, int grid, cudaStream_t stream, size_t min_smem) {
     if (n_chains <= 0) return cudaSuccess;
     const dim3 block(32 * warps);
-    const size_t smem = aeq_smem_bytes(na, warps, prm.period);
+    // min_smem reserves extra shared memory to cap the CTAs resident per SM
+    const size_t smem = std::max(aeq_smem_bytes(na, warps, prm.period), min_smem);
     const int n_items = 2 * n_chains;
     if (grid <= 0) grid = (n_items + warps - 1) / warps;
     if (na == 64)

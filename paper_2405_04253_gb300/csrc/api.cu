@@ -168,6 +168,8 @@ extern "C" fnt_status fnt_plan_create(const fnt_plan_desc *d, fnt_plan **out) {
     p->d = *d;
     p->device = device;
     cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device);
+    cudaDeviceGetAttribute(&p->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
+    cudaDeviceGetAttribute(&p->smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, p->device);
     int32_t init[16 * kAeqK] = {0};
     for (int s = 0; s < 4; ++s) init[(s * 4 + s) * kAeqK + kAeqK / 2] = (int32_t)((int64_t)d->tap_init * 65536);
     memcpy(p->h_init, init, sizeof init);
@@ -241,6 +243,21 @@ extern "C" fnt_status fnt_plan_set_pipeline(fnt_plan *p, int32_t chunks) {
     if (chunks < 1 || chunks > 16) return fail(FNT_ERR_INVALID, "chunks must be in [1, 16]");
     p->chunks = chunks;
     return FNT_OK;
+}
+
+extern "C" fnt_status fnt_plan_set_aeq_occupancy(fnt_plan *p, int32_t max_warps_per_sm) {
+    if (!p) return fail(FNT_ERR_INVALID, "null plan");
+    if (max_warps_per_sm < 0 || max_warps_per_sm > 64)
+        return fail(FNT_ERR_INVALID, "AEQ warps per SM must be in [0, 64]");
+    p->aeq_occupancy = max_warps_per_sm;
+    return FNT_OK;
+}
+
+size_t fnt::aeq_min_smem(const fnt_plan *p) {
+    if (p->aeq_occupancy <= 0 || p->smem_per_sm <= 0) return 0;
+    const int ctas = std::max(1, p->aeq_occupancy / p->aeq_warps);
+    const int per_cta = p->smem_per_sm / ctas - p->smem_reserved;
+    return per_cta > 0 ? (size_t)per_cta : 0;
 }
 
 extern "C" fnt_status fnt_plan_initial_taps(const fnt_plan *p, int32_t *state) {
@@ -600,7 +617,7 @@ static fnt_status launch_aeq_range(const fnt_plan *p, const Work &w, const char 
     const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
     AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d), p->tensor_gradient, p->d.aeq_freq_sum};
     cudaError_t e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(dev + w.off_chains) + c0, c1 - c0, prm,
-                               p->aeq_warps, 0, stream);
+                               p->aeq_warps, 0, stream, aeq_min_smem(p));
     return e == cudaSuccess ? FNT_OK : cuda_fail(e, "aeq kernel launch");
 }
 

@@ -20,6 +20,9 @@ struct fnt_plan {
     int chunks = 1;              // pipelined chunks of prepared chain batches (1 = off)
     int tensor_gradient = 0;     // AEQ gradient on the tensor cores (opt-in, same results)
     int cdc_pols_per_item = 0;   // CDC items: 0 auto, 1 one polarisation, 2 both
+    int aeq_occupancy = 0;       // AEQ warps per SM cap (0: as many as resources allow)
+    int smem_per_sm = 0;         // the device's shared memory per SM and per-CTA reserve
+    int smem_reserved = 0;
     cudaMemPool_t pool = nullptr;  // per-call work memory, kept mapped between calls
 };
 
@@ -84,6 +87,7 @@ cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, b
 size_t aeq_smem_bytes(int na, int warps, int period);
 cudaError_t aeq_configure();
 cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,
-                       int warps, int grid, cudaStream_t stream);
+                       int warps, int grid, cudaStream_t stream, size_t min_smem = 0);
+size_t aeq_min_smem(const fnt_plan *p);   // shared memory per AEQ CTA that enforces the occupancy cap
 
 }  // namespace fnt

@@ -176,7 +176,8 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
             if (e != cudaSuccess) return cuda_fail(e, "noalloc: copy initial taps");
         }
         AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d), p->tensor_gradient, p->d.aeq_freq_sum};
-        e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(base + kOffChains), nc, prm, p->aeq_warps, 0, stream);
+        e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(base + kOffChains), nc, prm, p->aeq_warps, 0, stream,
+                       aeq_min_smem(p));
         if (e != cudaSuccess) return cuda_fail(e, "noalloc: aeq kernel launch");
     }
     return FNT_OK;

@@ -528,6 +528,32 @@ def test_plan_initial_taps_equal_the_oracle_init(orc, tap_init):
     assert np.array_equal(o1.cpu().numpy(), o2.cpu().numpy())
 
 
+@pytest.mark.parametrize("occ,warps", [(4, 4), (12, 4), (20, 2)])
+def test_aeq_occupancy_cap_gives_the_same_bits(orc, occ, warps):
+    """Capping the AEQ warps per SM (shared memory reserved per CTA) changes
+    only residency: a batch of uneven frames with fresh taps gives the same
+    bits as without the cap, and a frame equals the oracle."""
+    rng = np.random.default_rng(44)
+    plan = F.Plan(mu_shift=9)
+    lens = [4096, 9000, 20000, 333, 60000]
+    fr = [synth.random_frame(rng, n, 2, int(rng.choice([5, 17, 19]))) for n in lens]
+    def run(cap):
+        plan.set_launch(aeq_warps=warps)
+        plan.set_aeq_occupancy(cap)
+        outs = [i16((F.chain_nsym(f.x.shape[0], f.taps.shape[0]), 4)) for f in fr]
+        F.cdc_aeq_run(plan, [F.Frame(dev(f.x), o, f.taps) for f, o in zip(fr, outs)])
+        torch.cuda.synchronize()
+        return [o.cpu().numpy() for o in outs]
+    base = run(0)
+    capped = run(occ)
+    for a, b in zip(base, capped):
+        assert np.array_equal(a, b)
+    ref, _ = orc.chain(fr[3].x, fr[3].taps, orc.ChainParams(mu_shift=9))
+    assert np.array_equal(capped[3], ref)
+    with pytest.raises(F.FntError):
+        plan.set_aeq_occupancy(65)
+
+
 def test_chain_full_size_cfg2_sampled_segments(orc):
     """The benchmark's workload at full size (2^21 samples per polarisation,
     segments of 864 with stream history, carried state), launched as bench.py

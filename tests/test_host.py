@@ -108,6 +108,14 @@ def test_version_and_defaults_without_gpu(libfnt):
     assert (d.n_cdc, d.alpha_cdc, d.n_aeq, d.alpha_aeq, d.aeq_taps) == (64, 4080, 32, 2, 16)
 
 
+def test_plan_setters_reject_a_null_plan_without_gpu(libfnt):
+    """Launch knobs validate their arguments on the host (no GPU needed)."""
+    libfnt.fnt_plan_set_aeq_occupancy.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    libfnt.fnt_plan_set_launch.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
+    assert libfnt.fnt_plan_set_aeq_occupancy(None, 8) == 1        # FNT_ERR_INVALID
+    assert libfnt.fnt_plan_set_launch(None, 4, 2) == 1
+
+
 def test_plan_rejects_invalid_radix_without_gpu():
     # eq. (4) is checked on the host before any device call
     import paper_2405_04253_gb300 as fnt
