@@ -218,3 +218,22 @@ def test_tab1_multiplication_counts():
     # the default step N - L + 1 spends fewer products per symbol
     assert fnt.op_counts(17)["cdc_mults_per_symbol"] == 128 / 24
     assert fnt.op_counts(17, n_aeq=64, alpha_aeq=4080)["aeq_mults_per_symbol"] == 32 * 64 / 48
+
+
+def test_request_records_marshal_pointers_and_sizes():
+    """fnt.Requests packs (link, in, n, out) into fnt_request records with the
+    buffers' addresses and sample counts, and keeps the buffers alive."""
+    import numpy as np
+    import paper_2405_04253_gb300 as fnt
+    xs = [np.zeros((n, 2, 2), np.int8) for n in (5, 0, 1234)]
+    outs = [np.zeros((max(1, n // 2), 4), np.int16) for n in (5, 0, 1234)]
+    r = fnt.Requests([3, 0, 7], xs, outs)
+    assert len(r) == 3 and r.rec.dtype == fnt.REQUEST_DTYPE
+    assert r.rec["link"].tolist() == [3, 0, 7]
+    assert r.rec["n"].tolist() == [5, 0, 1234]
+    assert r.rec["reserved"].tolist() == [0, 0, 0]
+    assert r.rec["in_"].tolist() == [x.ctypes.data for x in xs]
+    assert r.rec["out"].tolist() == [o.ctypes.data for o in outs]
+    assert r.bufs[2][0] is xs[2] and r.bufs[2][1] is outs[2]
+    r2 = fnt.Requests([1], xs[:1], outs[:1], ns=[4])
+    assert r2.rec["n"].tolist() == [4]
