@@ -239,6 +239,11 @@ typedef enum fnt_op { FNT_OP_CDC = 0, FNT_OP_AEQ = 1, FNT_OP_CHAIN = 2 } fnt_op;
 typedef struct fnt_batch fnt_batch;
 
 /*
+ * Prepared batches, launch knobs and the serving session below are execution
+ * machinery.  The paper defines none of them (it describes a hardware
+ * datapath); they schedule the operations of eqs. (1)-(8) and (6) defined
+ * above, and change no result.
+ *
  * Prepares a batch once for repeated launches: validates it, builds the work
  * lists (frames split into 32-block CDC items; AEQ chains or segments sorted
  * longest first), uploads them and allocates the intermediate buffers, all in
@@ -305,6 +310,7 @@ FNT_API fnt_status fnt_plan_set_aeq_occupancy(fnt_plan *plan, int32_t max_warps_
 /* The plan's initial AEQ taps (the state a frame without aeq_state, or a newly
  * configured serving link, starts from): HOST int32 [4 (S2)][4 (S1)][16],
  * zero except the centre tap of the four diagonal filters, tap_init << 16.
+ * The paper leaves the initial taps open; this is the usual centre-spike start.
  * Copying it into a frame's aeq_state starts that state's adaptation there. */
 FNT_API fnt_status fnt_plan_initial_taps(const fnt_plan *plan, int32_t *state);
 
