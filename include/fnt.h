@@ -49,7 +49,8 @@ typedef enum fnt_status {
     FNT_ERR_BUSY = 4,      /* session admission refused: memory cap or slots full */
     FNT_ERR_TIMEOUT = 5,   /* poll timed out with nothing completed */
     FNT_ERR_CUDA = 6,      /* a CUDA runtime call failed (detail in fnt_last_error) */
-    FNT_ERR_NOT_FOUND = 7  /* unknown link or ticket */
+    FNT_ERR_NOT_FOUND = 7, /* unknown link or ticket */
+    FNT_ERR_CANCELLED = 8  /* the request was cancelled before it was launched */
 } fnt_status;
 
 /* Copies the calling thread's last error text into buf (always NUL-terminated).
@@ -422,6 +423,31 @@ typedef struct fnt_request {
  * tickets[0..*n_admitted) their tickets (HOST arrays of n_reqs entries). */
 FNT_API fnt_status fnt_session_submit_many(fnt_session *s, const fnt_request *reqs, int32_t n_reqs,
                                    uint64_t *tickets, int32_t *n_admitted);
+
+/* Cancels an admitted request that has not been launched yet: it completes
+ * (through fnt_session_poll) with status FNT_ERR_CANCELLED, its memory is
+ * released, and its link's later frames run as if it had never been
+ * submitted.  FNT_ERR_NOT_FOUND when the ticket is unknown, already launched or
+ * already complete (a launched frame always runs to completion). */
+FNT_API fnt_status fnt_session_cancel(fnt_session *s, uint64_t ticket);
+
+/* Counters of a session since its creation (a snapshot). */
+typedef struct fnt_session_stats {
+    uint64_t admitted;        /* requests admitted */
+    uint64_t completed;       /* requests completed OK */
+    uint64_t failed;          /* requests completed with an error (not cancelled) */
+    uint64_t cancelled;       /* requests cancelled before launch */
+    uint64_t waves;           /* waves launched */
+    uint64_t chained_waves;   /* of which waited on the device for an earlier wave */
+    uint64_t wave_frames;     /* frames in all launched waves */
+    uint64_t max_wave;        /* largest wave, frames */
+    uint64_t arena_used;      /* bytes of the memory cap held now */
+    uint64_t arena_peak;      /* most bytes ever held */
+    int32_t queued;           /* admitted, not launched */
+    int32_t in_flight;        /* launched, not complete */
+} fnt_session_stats;
+
+FNT_API fnt_status fnt_session_get_stats(fnt_session *s, fnt_session_stats *out);
 
 /* Drives the scheduler and collects finished requests (at most max_done).  Waits
  * up to timeout_us for at least one completion (0 = do not wait); returns

@@ -15,11 +15,11 @@ import numpy as np
 from .build import LIB, build  # noqa: F401
 
 FNT_OK, FNT_ERR_INVALID, FNT_ERR_BOUND, FNT_ERR_NOMEM, FNT_ERR_BUSY, FNT_ERR_TIMEOUT, FNT_ERR_CUDA, \
-    FNT_ERR_NOT_FOUND = range(8)
+    FNT_ERR_NOT_FOUND, FNT_ERR_CANCELLED = range(9)
 OP_CDC, OP_AEQ, OP_CHAIN = 0, 1, 2
 
 _STATUS = {0: "FNT_OK", 1: "FNT_ERR_INVALID", 2: "FNT_ERR_BOUND", 3: "FNT_ERR_NOMEM", 4: "FNT_ERR_BUSY",
-           5: "FNT_ERR_TIMEOUT", 6: "FNT_ERR_CUDA", 7: "FNT_ERR_NOT_FOUND"}
+           5: "FNT_ERR_TIMEOUT", 6: "FNT_ERR_CUDA", 7: "FNT_ERR_NOT_FOUND", 8: "FNT_ERR_CANCELLED"}
 
 
 class FntError(RuntimeError):
@@ -56,6 +56,13 @@ class Completion(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("link", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("n_sym", ctypes.c_int64), ("submit_us", ctypes.c_double), ("start_us", ctypes.c_double),
                 ("done_us", ctypes.c_double)]
+
+
+class SessionStats(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("waves", ctypes.c_uint64), ("chained_waves", ctypes.c_uint64),
+                ("wave_frames", ctypes.c_uint64), ("max_wave", ctypes.c_uint64), ("arena_used", ctypes.c_uint64),
+                ("arena_peak", ctypes.c_uint64), ("queued", ctypes.c_int32), ("in_flight", ctypes.c_int32)]
 
 
 # fnt_request (batched session admission) and fnt_completion as numpy records
@@ -96,6 +103,8 @@ SIGNATURES = {
     "fnt_session_set_link": (_I32, [_VP, _I32, _VP, _I32]),
     "fnt_session_submit": (_I32, [_VP, _I32, _VP, _I64, _VP, ctypes.POINTER(ctypes.c_uint64)]),
     "fnt_session_submit_many": (_I32, [_VP, _VP, _I32, _VP, ctypes.POINTER(_I32)]),
+    "fnt_session_cancel": (_I32, [_VP, ctypes.c_uint64]),
+    "fnt_session_get_stats": (_I32, [_VP, ctypes.POINTER(SessionStats)]),
     "fnt_session_poll": (_I32, [_VP, _I32, ctypes.POINTER(Completion), _I32, ctypes.POINTER(_I32)]),
     "fnt_session_pending": (_I32, [_VP]),
     "fnt_session_get_link_state": (_I32, [_VP, _I32, _VP]),
@@ -400,6 +409,20 @@ class Session:
             out.append(dict(ticket=c.ticket, link=c.link, status=c.status, n_sym=c.n_sym, submit_us=c.submit_us,
                             start_us=c.start_us, done_us=c.done_us))
         return out
+
+    def cancel(self, ticket: int) -> bool:
+        """Cancels a request not launched yet (it completes as FNT_ERR_CANCELLED);
+        False when it is already launched, complete or unknown."""
+        st = lib().fnt_session_cancel(self.handle, int(ticket))
+        if st == FNT_ERR_NOT_FOUND:
+            return False
+        check(st)
+        return True
+
+    def stats(self) -> dict:
+        st = SessionStats()
+        check(lib().fnt_session_get_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in SessionStats._fields_}
 
     def pending(self) -> int:
         return int(lib().fnt_session_pending(self.handle))

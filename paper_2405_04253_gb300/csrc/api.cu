@@ -759,14 +759,17 @@ static fnt_status run(const fnt_plan *p, const fnt_frame_batch *b, int op, void 
 }  // namespace fnt
 
 extern "C" fnt_status fnt_cdc_run(const fnt_plan *p, const fnt_frame_batch *b, void *stream) {
+    Range trace("fnt_cdc_run");
     return run(p, b, FNT_OP_CDC, stream);
 }
 
 extern "C" fnt_status fnt_aeq_run(const fnt_plan *p, const fnt_frame_batch *b, void *stream) {
+    Range trace("fnt_aeq_run");
     return run(p, b, FNT_OP_AEQ, stream);
 }
 
 extern "C" fnt_status fnt_cdc_aeq_run(const fnt_plan *p, const fnt_frame_batch *b, void *stream) {
+    Range trace("fnt_cdc_aeq_run");
     return run(p, b, FNT_OP_CHAIN, stream);
 }
 
@@ -918,6 +921,7 @@ static fnt_status batch_launch_all(fnt_batch *bt, cudaStream_t stream);
 
 extern "C" fnt_status fnt_batch_launch(fnt_batch *bt, void *stream_) {
     if (!bt) return fail(FNT_ERR_INVALID, "null batch");
+    Range trace("fnt_batch_launch");
     cudaStream_t stream = (cudaStream_t)stream_;
     if (!bt->in_copy) return batch_launch_all(bt, stream);
     fnt_status st = start_input_copy(bt, stream);
@@ -960,6 +964,7 @@ static fnt_status batch_launch_all(fnt_batch *bt, cudaStream_t stream) {
 
 extern "C" fnt_status fnt_batch_launch_stage(fnt_batch *bt, int32_t stage, void *stream_) {
     if (!bt) return fail(FNT_ERR_INVALID, "null batch");
+    Range trace(stage == 0 ? "fnt_batch_launch_stage cdc" : "fnt_batch_launch_stage aeq");
     if (stage != 0 && stage != 1) return fail(FNT_ERR_INVALID, "stage must be 0 (CDC) or 1 (AEQ)");
     cudaStream_t stream = (cudaStream_t)stream_;
     // with the input copy on, the stage that reads the inputs copies them first

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <vector>
@@ -27,6 +28,15 @@ struct fnt_plan {
 };
 
 namespace fnt {
+
+// An NVTX range over a host-side scope (visible in Nsight Systems timelines;
+// without a tool attached the calls do next to nothing).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 fnt_status fail(fnt_status st, const char *fmt, ...);
 fnt_status check_device(const fnt_plan *p);   // FNT_ERR_INVALID unless the plan's device is current

@@ -69,6 +69,7 @@ using namespace fnt;
 
 extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame *f, void *stream_) {
     if (!p || !f) return fail(FNT_ERR_INVALID, "noalloc: null argument");
+    Range trace("fnt_cdc_aeq_run_noalloc");
     fnt_status dst = check_device(p);
     if (dst != FNT_OK) return dst;
     cudaStream_t stream = (cudaStream_t)stream_;

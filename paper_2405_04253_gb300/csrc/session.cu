@@ -66,6 +66,7 @@ class Arena {
         }
         return false;
     }
+    size_t used() const { return used_; }
     void release(size_t off, size_t bytes) {
         if (!bytes) return;
         used_ -= bytes;
@@ -154,6 +155,7 @@ struct fnt_session {
     std::vector<int> free_waves;
     uint64_t next_wave = 1;
     std::vector<char *> retired;          // outgrown table staging, freed at destroy
+    fnt_session_stats stats{};            // counters (queued / in_flight filled on read)
     std::deque<fnt_completion> done;
     uint64_t next_ticket = 1;
     int admitted = 0;                     // admitted and not yet returned by poll
@@ -327,6 +329,7 @@ void complete(fnt_session *ss, int wi, int status, double t, bool launch_failed)
         c.start_us = r.start_us;
         c.done_us = t;
         ss->done.push_back(c);
+        ++(status == FNT_OK ? ss->stats.completed : ss->stats.failed);
     }
     wave.reqs.clear();
     ss->free_waves.push_back(wi);
@@ -356,8 +359,17 @@ void form_wave(fnt_session *ss, int li, cudaEvent_t dep, std::vector<std::pair<d
         wave.reqs.push_back(r);
     }
     lane.wave = wi;
-    fnt_status st = launch_wave(ss, lane.stream, wave, dep);
-    if (st != FNT_OK) {
+    fnt_status st;
+    {
+        Range trace("fnt session wave");
+        st = launch_wave(ss, lane.stream, wave, dep);
+    }
+    if (st == FNT_OK) {
+        ++ss->stats.waves;
+        ss->stats.chained_waves += dep != nullptr;
+        ss->stats.wave_frames += wave.reqs.size();
+        ss->stats.max_wave = std::max<uint64_t>(ss->stats.max_wave, wave.reqs.size());
+    } else {
         // nothing of a failed wave is trusted: its requests complete with the error
         cudaStreamSynchronize(lane.stream);
         lane.wave = -1;
@@ -442,6 +454,8 @@ fnt_status admit(fnt_session *ss, int32_t link, const void *in, int64_t n, void 
     r.submit_us = now_us();
     lk.fifo.push_back(r);
     ++ss->admitted;
+    ++ss->stats.admitted;
+    ss->stats.arena_peak = std::max<uint64_t>(ss->stats.arena_peak, ss->arena.used());
     *ticket = r.ticket;
     return FNT_OK;
 }
@@ -536,6 +550,42 @@ extern "C" fnt_status fnt_session_submit_many(fnt_session *ss, const fnt_request
     }
     if (*n_admitted > 0) schedule(ss);
     return st;
+}
+
+extern "C" fnt_status fnt_session_cancel(fnt_session *ss, uint64_t ticket) {
+    if (!ss) return fail(FNT_ERR_INVALID, "null session");
+    std::lock_guard<std::mutex> g(ss->mu);
+    for (LinkState &lk : ss->links) {
+        for (auto it = lk.fifo.begin(); it != lk.fifo.end(); ++it) {
+            if (it->ticket != ticket) continue;
+            ss->arena.release(it->off, it->bytes);
+            fnt_completion c{};
+            c.ticket = it->ticket;
+            c.link = it->link;
+            c.status = FNT_ERR_CANCELLED;
+            c.submit_us = it->submit_us;
+            c.done_us = now_us();
+            ss->done.push_back(c);
+            ++ss->stats.cancelled;
+            lk.fifo.erase(it);
+            return FNT_OK;
+        }
+    }
+    return fail(FNT_ERR_NOT_FOUND, "cancel: ticket %llu is not waiting for launch", (unsigned long long)ticket);
+}
+
+extern "C" fnt_status fnt_session_get_stats(fnt_session *ss, fnt_session_stats *out) {
+    if (!ss || !out) return fail(FNT_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> g(ss->mu);
+    *out = ss->stats;
+    out->arena_used = ss->arena.used();
+    out->queued = 0;
+    out->in_flight = 0;
+    for (const LinkState &lk : ss->links) {
+        out->queued += (int32_t)lk.fifo.size();
+        out->in_flight += lk.inflight;
+    }
+    return FNT_OK;
 }
 
 extern "C" fnt_status fnt_session_poll(fnt_session *ss, int32_t timeout_us, fnt_completion *done, int32_t max_done,

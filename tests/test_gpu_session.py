@@ -405,3 +405,36 @@ def test_session_tiny_and_empty_frames_in_a_burst(orc):
     for l in range(len(links)):
         assert np.array_equal(s.get_link_state(l), Tref[l])
     s.close()
+
+
+def test_session_cancel_a_queued_request_and_stats(orc):
+    """One main lane and four chain lanes: eight frames of one link admitted
+    together launch five waves at once and queue three.  A queued one can be
+    cancelled (it completes as FNT_ERR_CANCELLED and the link's other frames
+    equal the oracle run without it); a launched one cannot.  The session's
+    counters account for all of it."""
+    rng = np.random.default_rng(33)
+    links = make_links(rng, 1)
+    frames = [(0, rng.integers(-16, 16, (6000, 2, 2)).astype(np.int8)) for _ in range(8)]
+    s = F.Session(F.Plan(mu_shift=MU), 1, 1 << 28, 1)
+    s.set_link(0, links[0])
+    xs, outs = _device_frames(frames, links)
+    tk = s.submit_many(F.Requests([0] * 8, xs, outs))
+    st = s.stats()
+    assert (st["admitted"], st["waves"], st["chained_waves"], st["queued"], st["in_flight"]) == (8, 5, 4, 3, 5)
+    assert not s.cancel(tk[0])                 # launched: runs to completion
+    assert s.cancel(tk[6])                     # queued
+    assert not s.cancel(tk[6])                 # already cancelled
+    done = {c[0]: c[2] for c in _drain(s, 8)}
+    assert done[tk[6]] == F.FNT_ERR_CANCELLED
+    assert all(done[t] == F.FNT_OK for i, t in enumerate(tk) if i != 6)
+    kept = [i for i in range(8) if i != 6]
+    ref, Tref = oracle_sequential(orc, links, [frames[i] for i in kept])
+    for j, i in enumerate(kept):
+        assert np.array_equal(outs[i].cpu().numpy(), ref[j]), i
+    assert np.array_equal(s.get_link_state(0), Tref[0])
+    st = s.stats()
+    assert (st["completed"], st["cancelled"], st["failed"], st["queued"], st["in_flight"]) == (7, 1, 0, 0, 0)
+    assert st["arena_used"] == 0 and st["arena_peak"] > 0
+    assert (st["wave_frames"], st["max_wave"]) == (7, 1)
+    s.close()

@@ -77,6 +77,7 @@ def test_binding_struct_layouts_match_the_header():
         "fnt_frame_batch": (fnt.BatchC, None),
         "fnt_op_counts": (fnt.OpCounts, None),
         "fnt_completion": (fnt.Completion, None),
+        "fnt_session_stats": (fnt.SessionStats, None),
     }
     for struct, (cls, rename) in ctypes_structs.items():
         names = [f[0] for f in cls._fields_]
