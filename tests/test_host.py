@@ -238,3 +238,51 @@ def test_request_records_marshal_pointers_and_sizes():
     assert r.bufs[2][0] is xs[2] and r.bufs[2][1] is outs[2]
     r2 = fnt.Requests([1], xs[:1], outs[:1], ns=[4])
     assert r2.rec["n"].tolist() == [4]
+
+
+def test_every_entry_point_rejects_null_handles_without_gpu():
+    """The ABI never crashes on a null handle: every status-returning call
+    returns FNT_ERR_INVALID (destroy calls: FNT_OK), and the counters of a null
+    object read as zero, all before any CUDA call."""
+    import paper_2405_04253_gb300 as fnt
+    L = fnt.lib()
+    inv = fnt.FNT_ERR_INVALID
+    calls = {
+        "fnt_plan_create": (None, None),
+        "fnt_op_counts_for": (None, 17, None),
+        "fnt_cdc_run": (None, None, None),
+        "fnt_aeq_run": (None, None, None),
+        "fnt_cdc_aeq_run": (None, None, None),
+        "fnt_batch_create": (None, None, 2, 0, None),
+        "fnt_batch_launch": (None, None),
+        "fnt_batch_set_input_copy": (None, 1),
+        "fnt_batch_launch_stage": (None, 0, None),
+        "fnt_plan_set_launch": (None, 4, 2),
+        "fnt_plan_set_pipeline": (None, 1),
+        "fnt_plan_set_aeq_occupancy": (None, 8),
+        "fnt_plan_initial_taps": (None, None),
+        "fnt_plan_set_cdc_items": (None, 0),
+        "fnt_plan_set_tensor_gradient": (None, 0),
+        "fnt_cdc_aeq_run_noalloc": (None, None, None),
+        "fnt_session_create": (None, 1, 1 << 20, 1, None),
+        "fnt_session_set_link": (None, 0, None, 5),
+        "fnt_session_submit": (None, 0, None, 0, None, None),
+        "fnt_session_submit_many": (None, None, 0, None, None),
+        "fnt_session_cancel": (None, 1),
+        "fnt_session_get_stats": (None, None),
+        "fnt_session_poll": (None, 0, None, 0, None),
+        "fnt_session_get_link_state": (None, 0, None),
+        "fnt_session_set_link_state": (None, 0, None),
+        "fnt_session_inject_failures": (None, 1),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == inv, name
+    for name in ("fnt_plan_destroy", "fnt_batch_destroy", "fnt_session_destroy"):
+        assert getattr(L, name)(None) == fnt.FNT_OK, name
+    assert L.fnt_batch_kernel_count(None) == 0
+    assert L.fnt_session_pending(None) == 0
+    assert fnt.last_error()                  # the last failure left its text
+    decl = set(header_functions())
+    covered = set(calls) | {"fnt_plan_destroy", "fnt_batch_destroy", "fnt_session_destroy", "fnt_batch_kernel_count",
+                            "fnt_session_pending", "fnt_last_error", "fnt_version", "fnt_plan_desc_default"}
+    assert decl <= covered, decl - covered
