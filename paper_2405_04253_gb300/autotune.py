@@ -14,6 +14,22 @@ import os
 from . import OP_CHAIN, Batch, Plan
 
 CANDIDATES = (1, 2, 3, 4)
+_SRC_TAG = None
+
+
+def _src_tag() -> str:
+    """Short hash of the library's sources: a cache entry written by another
+    build of the kernels is not reused."""
+    global _SRC_TAG
+    if _SRC_TAG is None:
+        import hashlib
+        csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+        h = hashlib.sha256()
+        for name in sorted(os.listdir(csrc)):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+        _SRC_TAG = h.hexdigest()[:12]
+    return _SRC_TAG
 OCCUPANCY = (0, 12, 16, 20)          # AEQ warps per SM cap (0: none)
 
 
@@ -22,7 +38,7 @@ def _key(plan: Plan, frames, op: int) -> str:
     lens = sorted(int(f.n) for f in frames)
     total = sum(lens)
     return (f"op{op}_n{len(frames)}_tot{total}_max{lens[-1] if lens else 0}_aeq{d.n_aeq}"
-            f"_seg{d.aeq_segment}_{d.aeq_warmup}_p{d.aeq_update_period}")
+            f"_seg{d.aeq_segment}_{d.aeq_warmup}_p{d.aeq_update_period}_src{_src_tag()}")
 
 
 def _time_stage(batch: Batch, stage: int, reps: int, stream) -> float:

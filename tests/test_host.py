@@ -286,3 +286,17 @@ def test_every_entry_point_rejects_null_handles_without_gpu():
     covered = set(calls) | {"fnt_plan_destroy", "fnt_batch_destroy", "fnt_session_destroy", "fnt_batch_kernel_count",
                             "fnt_session_pending", "fnt_last_error", "fnt_version", "fnt_plan_desc_default"}
     assert decl <= covered, decl - covered
+
+
+def test_autotune_key_follows_shape_and_sources():
+    """The launch-shape cache key changes with the workload's shape and with
+    the library's sources (a stale entry is never reused)."""
+    from types import SimpleNamespace
+    from paper_2405_04253_gb300 import autotune
+    plan = SimpleNamespace(desc=SimpleNamespace(n_aeq=32, aeq_segment=0, aeq_warmup=0, aeq_update_period=1))
+    fr = [SimpleNamespace(n=n) for n in (4096, 70000, 9000)]
+    k1 = autotune._key(plan, fr, 2)
+    assert k1 == autotune._key(plan, list(reversed(fr)), 2)
+    assert k1 != autotune._key(plan, fr[:2], 2)
+    assert k1 != autotune._key(plan, fr, 1)
+    assert k1.endswith("_src" + autotune._src_tag()) and len(autotune._src_tag()) == 12
