@@ -164,6 +164,24 @@ def test_aeq_extreme_taps(orc, na, alpha, tensor):
     assert np.abs(got.astype(np.int64)).max() >= 32767          # saturated outputs were covered
 
 
+@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
+@pytest.mark.parametrize("xv", [-1, 15, -16])
+def test_aeq_constant_worst_case_inputs(orc, na, alpha, tensor, xv):
+    """Constant inputs at the special residue (-1 maps to 65536 in every
+    transform input) and at both ends of the 5-bit range, adapting from the
+    plan's taps and from random 14-bit taps."""
+    rng = np.random.default_rng(45)
+    x = np.full((900, 4), xv, dtype=np.int8)
+    Trand = (rng.integers(-8192, 8192, (4, 4, 16)).astype(np.int64) << 16).astype(np.int32)
+    for T0 in (orc.aeq_init_taps(16, 2048), Trand):
+        plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=20)
+        plan.set_tensor_gradient(tensor)
+        got, Tg = run_aeq(plan, x, T0)
+        ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=20, rde_a=64)
+        assert np.array_equal(got, ref) and np.array_equal(Tg, Tr)
+
+
 def test_aeq_no_state_uses_plan_init(orc):
     rng = np.random.default_rng(4)
     x = rng.integers(-16, 16, (900, 4)).astype(np.int8)
