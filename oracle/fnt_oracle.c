@@ -20,11 +20,14 @@
  *   orc_requant_decimate                pinned (hand-worked cases)
  *   orc_aeq, mu = 0                     pinned (equals exact 4x4 integer MIMO
  *                                       convolution, computed by numpy)
- *   orc_aeq, adaptive                   pinned through its one-block gradient
- *                                       against a float64 finite-difference
- *                                       derivative of the RDE cost; the long-run
- *                                       recurrence beyond that is checked by
- *                                       invariants only
+ *   orc_aeq, adaptive                   pinned: the one-block gradient against a
+ *                                       float64 finite-difference derivative of
+ *                                       the RDE cost; the gradient summed over
+ *                                       many blocks (x[t-k] across block
+ *                                       boundaries and into the input history,
+ *                                       whole runs and segments) against a numpy
+ *                                       closed form of eq. (6); the update
+ *                                       period rebuilt period by period
  */
 #include "fnt_oracle.h"
 

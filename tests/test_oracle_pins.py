@@ -451,3 +451,99 @@ def test_aeq_freq_sum_exact_where_bound_holds_and_guarded_mode_always(orc):
             assert np.array_equal(a, c) and np.array_equal(Ta, Tc)
     with pytest.raises(ValueError):
         orc.aeq(x, T_small, 32, 2, use_fnt=False, freq_sum=1)   # no wrap to model without transforms
+
+
+def _gradient_closed_form(xh, W, hist, A, S=None):
+    """Eq. (6) summed over a whole run with the taps held fixed, from numpy alone.
+
+    xh: int [hist + n, 4]; its first `hist` rows are input history (no output),
+    zeros before them.  z comes from the exact 4x4 MIMO convolution (numpy),
+    e from the 16QAM ring rule, and
+        G[S2][S1][k] = sum_t e_p(S2)[t] z_S2[t] x_S1[t - k]
+    over every output time t of the run, x reaching back across block
+    boundaries and into the history.  With S given, the inputs before each
+    block's first time are zeroed instead: the planted mistake of a gradient
+    that forgets the previous block."""
+    xh = xh.astype(np.int64)
+    n = xh.shape[0] - hist
+    K = W.shape[2]
+    y = np.zeros((n, 4), np.int64)
+    for s2 in range(4):
+        for s1 in range(4):
+            y[:, s2] += np.convolve(xh[:, s1], W[s2, s1].astype(np.int64))[hist:hist + n]
+    z = np.clip(y >> 7, -32768, 32767)
+    e = np.zeros((n, 2), np.int64)
+    for p in range(2):
+        r2 = z[:, 2 * p] ** 2 + z[:, 2 * p + 1] ** 2
+        R = np.where(r2 < 6 * A * A, 2 * A * A, np.where(r2 < 14 * A * A, 10 * A * A, 18 * A * A))
+        e[:, p] = R - r2
+    G = np.zeros((4, 4, K), np.int64)
+    t = np.arange(n)
+    for k in range(K):
+        src = hist + t - k
+        xv = np.where(src[:, None] >= 0, xh[np.maximum(src, 0)], 0)
+        if S is not None:
+            xv = np.where(((t - k) >= (t // S) * S)[:, None], xv, 0)
+        for s2 in range(4):
+            G[s2, :, k] = (e[:, s2 // 2] * z[:, s2])[:, None].T @ xv
+    return z, G
+
+
+@pytest.mark.parametrize("N,alpha,n,hist", [(32, 2, 16 * 5 + 7, 0), (32, 2, 16 * 6 + 3, 16),
+                                            (64, 4080, 48 * 4 + 13, 0), (64, 4080, 48 * 5 + 1, 11)])
+def test_aeq_multiblock_gradient_closed_form(orc, N, alpha, n, hist):
+    """Eq. (6) across blocks: at m = 0 and an update period of at least the
+    block count, the taps stay fixed for the whole run and one final update
+    adds the summed gradient, so T_out - T0 must equal the numpy closed form
+    over all the run's times, whose x[t - k] crosses block boundaries and
+    reaches into the input history.  Four or more blocks, ragged tails, both
+    transform sizes.  The same closed form with each block's earlier inputs
+    zeroed (a gradient that forgets the previous block) must differ."""
+    K, A = 16, 8
+    rng = np.random.default_rng(1000 + N + n + hist)
+    xh = rng.integers(-4, 5, (hist + n, 4)).astype(np.int8)
+    W = rng.integers(-40, 41, (4, 4, K)).astype(np.int64)
+    for s in range(4):
+        W[s, s, K // 2] = 1024
+    T0 = (W << 16).astype(np.int32) + rng.integers(0, 1 << 16, W.shape).astype(np.int32)
+    never = 1 << 30
+    out, T1 = orc.aeq(xh, T0, N, alpha, mu_shift=0, rde_a=A, period=never, hist=hist)
+    z, G = _gradient_closed_form(xh, W, hist, A)
+    assert np.array_equal(out, z)
+    assert np.abs(T0.astype(np.int64) + G).max() < (1 << 29) - 1      # no clamp
+    assert (G != 0).all() or np.count_nonzero(G) > 200
+    assert np.array_equal(T1.astype(np.int64) - T0, G)
+    _, G_forget = _gradient_closed_form(xh, W, hist, A, S=N - K)
+    assert not np.array_equal(G_forget, G)
+    if hist:
+        xz = xh.copy()
+        xz[:hist] = 0
+        _, G_nohist = _gradient_closed_form(xz, W, hist, A)
+        assert not np.array_equal(G_nohist, G)
+
+
+@pytest.mark.parametrize("N,alpha,seg_len,warmup", [(32, 2, 100, 40), (64, 4080, 150, 60)])
+def test_aeq_segment_gradient_closed_form(orc, N, alpha, seg_len, warmup):
+    """The same closed form for the last segment of a segmented run: it starts
+    `warmup` symbols before its output segment, from T0, and reads the K
+    stream symbols before its start as history; its final taps are T0 plus the
+    summed gradient over its run."""
+    K, A = 16, 8
+    n = 3 * seg_len + 17
+    rng = np.random.default_rng(77 + N)
+    x = rng.integers(-4, 5, (n, 4)).astype(np.int8)
+    W = rng.integers(-40, 41, (4, 4, K)).astype(np.int64)
+    for s in range(4):
+        W[s, s, K // 2] = 1024
+    T0 = (W << 16).astype(np.int32)
+    never = 1 << 30
+    _, Tout = orc.aeq_segmented(x, T0, N, alpha, mu_shift=0, rde_a=A, seg_len=seg_len, warmup=warmup,
+                                period=never)
+    keep = (n - 1) // seg_len * seg_len
+    begin = keep - warmup
+    hist = min(begin, K)
+    z, G = _gradient_closed_form(x[begin - hist:n], W, hist, A)
+    assert np.abs(T0.astype(np.int64) + G).max() < (1 << 29) - 1
+    assert np.array_equal(Tout.astype(np.int64) - T0, G)
+    _, G_forget = _gradient_closed_form(x[begin - hist:n], W, hist, A, S=N - K)
+    assert not np.array_equal(G_forget, G)
