@@ -308,6 +308,15 @@ FNT_API fnt_status fnt_plan_set_pipeline(fnt_plan *plan, int32_t chunks);
  * it.  FNT_ERR_INVALID outside [0, 64]. */
 FNT_API fnt_status fnt_plan_set_aeq_occupancy(fnt_plan *plan, int32_t max_warps_per_sm);
 
+/* Picks the AEQ kernel of later launches of this plan: 1 = one warp per (chain,
+ * polarisation), the throughput layout for many chains; 2 = one CTA per (chain,
+ * polarisation), which spreads each block of the serial recurrence of eq. (6)
+ * (section "Proposed FNT-CDC&AEQ structure") over 288 threads and cuts the time
+ * per block of a lone chain; 0 (default) = 2 when the launch's chains fit one
+ * CTA per SM, else 1.  Plans with aeq_freq_sum != 0 always use 1.  Results do
+ * not depend on it.  FNT_ERR_INVALID outside [0, 2]. */
+FNT_API fnt_status fnt_plan_set_aeq_kernel(fnt_plan *plan, int32_t kind);
+
 /* The plan's initial AEQ taps (the state a frame without aeq_state, or a newly
  * configured serving link, starts from): HOST int32 [4 (S2)][4 (S1)][16],
  * zero except the centre tap of the four diagonal filters, tap_init << 16.

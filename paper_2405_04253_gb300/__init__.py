@@ -88,6 +88,7 @@ SIGNATURES = {
     "fnt_plan_set_cdc_items": (_I32, [_VP, _I32]),
     "fnt_plan_initial_taps": (_I32, [_VP, _VP]),
     "fnt_plan_set_aeq_occupancy": (_I32, [_VP, _I32]),
+    "fnt_plan_set_aeq_kernel": (_I32, [_VP, _I32]),
     "fnt_op_counts_for": (_I32, [ctypes.POINTER(PlanDesc), _I32, ctypes.POINTER(OpCounts)]),
     "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
     "fnt_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
@@ -203,6 +204,11 @@ class Plan:
     def set_aeq_occupancy(self, max_warps_per_sm: int):
         """Caps the AEQ warps resident per SM (0 = no cap); same results."""
         check(lib().fnt_plan_set_aeq_occupancy(self.handle, int(max_warps_per_sm)))
+
+    def set_aeq_kernel(self, kind: int):
+        """AEQ kernel: 1 a warp per (chain, polarisation), 2 a CTA per one,
+        0 automatic; same results."""
+        check(lib().fnt_plan_set_aeq_kernel(self.handle, int(kind)))
 
     def initial_state(self) -> np.ndarray:
         """The plan's initial AEQ taps, int32 [4 (S2)][4 (S1)][16]."""

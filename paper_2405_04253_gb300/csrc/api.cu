@@ -122,6 +122,8 @@ static fnt_status configure_kernels(int device) {
     if (e != cudaSuccess) return cuda_fail(e, "cdc_configure");
     e = aeq_configure();
     if (e != cudaSuccess) return cuda_fail(e, "aeq_configure");
+    e = aeq_serial_configure();
+    if (e != cudaSuccess) return cuda_fail(e, "aeq_serial_configure");
     g_configured.insert(device);
     return FNT_OK;
 }
@@ -258,6 +260,28 @@ size_t fnt::aeq_min_smem(const fnt_plan *p) {
     const int ctas = std::max(1, p->aeq_occupancy / p->aeq_warps);
     const int per_cta = p->smem_per_sm / ctas - p->smem_reserved;
     return per_cta > 0 ? (size_t)per_cta : 0;
+}
+
+extern "C" fnt_status fnt_plan_set_aeq_kernel(fnt_plan *p, int32_t kind) {
+    if (!p) return fail(FNT_ERR_INVALID, "null plan");
+    if (kind < 0 || kind > 2) return fail(FNT_ERR_INVALID, "AEQ kernel must be 0 (auto), 1 or 2");
+    p->aeq_kernel = kind;
+    return FNT_OK;
+}
+
+// The CTA-per-chain kernel holds one (chain, polarisation) per SM: it is taken
+// when that many fit in one wave, and only for per-pair inverse transforms.
+bool fnt::aeq_use_serial(const fnt_plan *p, int n_chains) {
+    if (p->d.aeq_freq_sum != 0 || p->aeq_kernel == 1) return false;
+    if (p->aeq_kernel == 2) return true;
+    return 2 * (int64_t)n_chains <= (int64_t)p->n_sm * kSerialCtasPerSm;
+}
+
+cudaError_t fnt::aeq_launch_for(const fnt_plan *p, const DevFrame *frames, const AeqChain *chains, int n_chains,
+                                cudaStream_t stream) {
+    AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d), p->tensor_gradient, p->d.aeq_freq_sum};
+    if (aeq_use_serial(p, n_chains)) return aeq_serial_launch(p->d.n_aeq, frames, chains, n_chains, prm, 0, stream);
+    return aeq_launch(p->d.n_aeq, frames, chains, n_chains, prm, p->aeq_warps, 0, stream, aeq_min_smem(p));
 }
 
 extern "C" fnt_status fnt_plan_initial_taps(const fnt_plan *p, int32_t *state) {
@@ -615,9 +639,7 @@ static fnt_status launch_aeq_range(const fnt_plan *p, const Work &w, const char 
                                    cudaStream_t stream) {
     if (c1 <= c0) return FNT_OK;
     const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
-    AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d), p->tensor_gradient, p->d.aeq_freq_sum};
-    cudaError_t e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(dev + w.off_chains) + c0, c1 - c0, prm,
-                               p->aeq_warps, 0, stream, aeq_min_smem(p));
+    cudaError_t e = aeq_launch_for(p, frames, (const AeqChain *)(dev + w.off_chains) + c0, c1 - c0, stream);
     return e == cudaSuccess ? FNT_OK : cuda_fail(e, "aeq kernel launch");
 }
 

@@ -22,6 +22,7 @@ struct fnt_plan {
     int tensor_gradient = 0;     // AEQ gradient on the tensor cores (opt-in, same results)
     int cdc_pols_per_item = 0;   // CDC items: 0 auto, 1 one polarisation, 2 both
     int aeq_occupancy = 0;       // AEQ warps per SM cap (0: as many as resources allow)
+    int aeq_kernel = 0;          // AEQ kernel: 0 auto, 1 a warp per chain, 2 a CTA per chain
     int smem_per_sm = 0;         // the device's shared memory per SM and per-CTA reserve
     int smem_reserved = 0;
     cudaMemPool_t pool = nullptr;  // per-call work memory, kept mapped between calls
@@ -86,6 +87,7 @@ int work_kernel_count(const Work &w);
 
 // kernels
 constexpr int kCdcCtasPerSm = 3;     // cdc_kernel's __launch_bounds__ minimum
+constexpr int kSerialCtasPerSm = 1;  // aeq_serial_kernel CTAs resident per SM (registers)
 size_t cdc_smem_bytes(int warps);
 int cdc_mults_per_block();
 int cdc_butterflies_per_block();
@@ -99,5 +101,15 @@ cudaError_t aeq_configure();
 cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,
                        int warps, int grid, cudaStream_t stream, size_t min_smem = 0);
 size_t aeq_min_smem(const fnt_plan *p);   // shared memory per AEQ CTA that enforces the occupancy cap
+// The CTA-per-chain AEQ kernel (aeq_serial.cu): few long chains, latency per block.
+size_t aeq_serial_smem_bytes(int na);
+cudaError_t aeq_serial_configure();
+cudaError_t aeq_serial_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,
+                              int grid, cudaStream_t stream);
+// Whether a launch of n_chains chains takes the CTA-per-chain kernel.
+bool aeq_use_serial(const fnt_plan *p, int n_chains);
+// Launches the AEQ kernel the plan picks for n_chains chains.
+cudaError_t aeq_launch_for(const fnt_plan *p, const DevFrame *frames, const AeqChain *chains, int n_chains,
+                           cudaStream_t stream);
 
 }  // namespace fnt

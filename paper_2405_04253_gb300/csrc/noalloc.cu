@@ -176,9 +176,7 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
             e = cudaMemcpyAsync(base + kOffInit, f->aeq_state, kStateBytes, cudaMemcpyDeviceToDevice, stream);
             if (e != cudaSuccess) return cuda_fail(e, "noalloc: copy initial taps");
         }
-        AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d), p->tensor_gradient, p->d.aeq_freq_sum};
-        e = aeq_launch(p->d.n_aeq, frames, (const AeqChain *)(base + kOffChains), nc, prm, p->aeq_warps, 0, stream,
-                       aeq_min_smem(p));
+        e = aeq_launch_for(p, frames, (const AeqChain *)(base + kOffChains), nc, stream);
         if (e != cudaSuccess) return cuda_fail(e, "noalloc: aeq kernel launch");
     }
     return FNT_OK;

@@ -113,6 +113,19 @@ def test_cdc_rejects_bad_frames():
 
 # --------------------------------------------------------------------- AEQ -----
 
+# AEQ paths: (kernel, tensor-core gradient).  "warp" is one warp per (chain,
+# polarisation), "cta" one CTA per (chain, polarisation); all give the same bits.
+AEQ_PATHS = {"warp": (1, False), "warp-mma": (1, True), "cta": (2, False)}
+
+
+def aeq_plan(path, **kw):
+    plan = F.Plan(**kw)
+    kernel, tensor = AEQ_PATHS[path]
+    plan.set_aeq_kernel(kernel)
+    plan.set_tensor_gradient(tensor)
+    return plan
+
+
 def run_aeq(plan, x, T=None):
     xd = dev(x)
     out = i16((x.shape[0], 4))
@@ -122,25 +135,24 @@ def run_aeq(plan, x, T=None):
     return out.cpu().numpy(), (None if st is None else st.cpu().numpy())
 
 
-@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("path", list(AEQ_PATHS))
 @pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
 @pytest.mark.parametrize("n,mu", [(1000, 8), (333, 12), (16, 8), (5, 8), (2000, 63), (4096 + 3, 6)])
-def test_aeq_matches_oracle(orc, na, alpha, n, mu, tensor):
+def test_aeq_matches_oracle(orc, na, alpha, n, mu, path):
     rng = np.random.default_rng(na * 1000 + n + mu)
     x = rng.integers(-16, 16, (n, 4)).astype(np.int8)
     T0 = orc.aeq_init_taps(16, 2048)
     T0 = T0 + rng.integers(-(1 << 20), 1 << 20, T0.shape).astype(np.int32)
-    plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=mu, rde_a=64)
-    plan.set_tensor_gradient(tensor)
+    plan = aeq_plan(path, n_aeq=na, alpha_aeq=alpha, mu_shift=mu, rde_a=64)
     got, Tg = run_aeq(plan, x, T0)
     ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=mu, rde_a=64)
     assert np.array_equal(got, ref)
     assert np.array_equal(Tg, Tr)
 
 
-@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("path", list(AEQ_PATHS))
 @pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
-def test_aeq_extreme_taps(orc, na, alpha, tensor):
+def test_aeq_extreme_taps(orc, na, alpha, path):
     """Saturated outputs (|z| = 32767 / 32768), |e| near 2^31 and inputs at both
     ends of the 5-bit range: the largest e z the gradient can see."""
     rng = np.random.default_rng(3)
@@ -156,18 +168,17 @@ def test_aeq_extreme_taps(orc, na, alpha, tensor):
         xs.append(x2)
     for xi, T0 in zip(xs, cases):
         for mu, a in ((30, 4096), (40, 1)):
-            plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=mu, rde_a=a)
-            plan.set_tensor_gradient(tensor)
+            plan = aeq_plan(path, n_aeq=na, alpha_aeq=alpha, mu_shift=mu, rde_a=a)
             got, Tg = run_aeq(plan, xi, T0)
             ref, Tr = orc.aeq(xi, T0, na, alpha, mu_shift=mu, rde_a=a)
             assert np.array_equal(got, ref) and np.array_equal(Tg, Tr)
     assert np.abs(got.astype(np.int64)).max() >= 32767          # saturated outputs were covered
 
 
-@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("path", list(AEQ_PATHS))
 @pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
 @pytest.mark.parametrize("xv", [-1, 15, -16])
-def test_aeq_constant_worst_case_inputs(orc, na, alpha, tensor, xv):
+def test_aeq_constant_worst_case_inputs(orc, na, alpha, path, xv):
     """Constant inputs at the special residue (-1 maps to 65536 in every
     transform input) and at both ends of the 5-bit range, adapting from the
     plan's taps and from random 14-bit taps."""
@@ -175,8 +186,7 @@ def test_aeq_constant_worst_case_inputs(orc, na, alpha, tensor, xv):
     x = np.full((900, 4), xv, dtype=np.int8)
     Trand = (rng.integers(-8192, 8192, (4, 4, 16)).astype(np.int64) << 16).astype(np.int32)
     for T0 in (orc.aeq_init_taps(16, 2048), Trand):
-        plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=20)
-        plan.set_tensor_gradient(tensor)
+        plan = aeq_plan(path, n_aeq=na, alpha_aeq=alpha, mu_shift=20)
         got, Tg = run_aeq(plan, x, T0)
         ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=20, rde_a=64)
         assert np.array_equal(got, ref) and np.array_equal(Tg, Tr)
@@ -257,18 +267,17 @@ def test_chain_freq_sum_guarded_segmented(orc):
     assert np.array_equal(st.cpu().numpy(), Tr)
 
 
-@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("path", list(AEQ_PATHS))
 @pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
 @pytest.mark.parametrize("period,n", [(2, 1000), (3, 333), (5, 4099), (64, 5000), (64, 700), (4, 16)])
-def test_aeq_update_period_matches_oracle(orc, na, alpha, period, n, tensor):
+def test_aeq_update_period_matches_oracle(orc, na, alpha, period, n, path):
     """Update period P: the summed gradient of P blocks is applied after every
     P-th block and the last; the taps (and their cached spectra) are fixed in
     between."""
     rng = np.random.default_rng(na + 7 * period + n)
     x = rng.integers(-16, 16, (n, 4)).astype(np.int8)
     T0 = orc.aeq_init_taps(16, 2048) + rng.integers(-(1 << 20), 1 << 20, (4, 4, 16)).astype(np.int32)
-    plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=12, aeq_update_period=period)
-    plan.set_tensor_gradient(tensor)
+    plan = aeq_plan(path, n_aeq=na, alpha_aeq=alpha, mu_shift=12, aeq_update_period=period)
     got, Tg = run_aeq(plan, x, T0)
     ref, Tr = orc.aeq(x, T0, na, alpha, mu_shift=12, rde_a=64, period=period)
     assert np.array_equal(got, ref)
