@@ -65,24 +65,31 @@ struct SerCfg {
     static constexpr int XBLK = 4 * S1STR;
     static constexpr int TP = R + 4;                        // transpose row (one n')
     static constexpr int TT = NP * TP + 8;                  // transpose rows of one task
-    static constexpr int TROW = K + 4;                      // master-tap row
-    static constexpr int PROW = SA + 4;                     // partial-output row
-    static constexpr int NPW = 16 * R / 32;                 // warps of phase 1
+    static constexpr int WROW = K + 4;                      // split-tap row [filter][group]
+    // decoded outputs [task][PROW]; the tasks of output 1 sit 16 words further,
+    // so that the two outputs of a symbol are read from opposite bank halves
+    static constexpr int PROW = SA + 8;
     static constexpr int NCONS = 256;                       // consumer threads
     static constexpr int NTHR = NCONS + 32;                 // + the producer warp
-    static constexpr int GSYM = SA / 8;                     // gradient symbols per thread
+    // gradient layout: at N = 64 a thread takes one tap of the four filters of
+    // an output over 1/8 of the block's symbols (three shuffle stages); at N = 32
+    // one tap of one filter over half of them (one shuffle stage)
+    static constexpr bool G4 = NA == 64;
+    static constexpr int GSYM = G4 ? SA / 8 : SA / 2;       // gradient symbols per thread
     // shared memory (words); every region a multiple of 4 words
-    static constexpr int O_TAPS = 0;
-    static constexpr int O_XF = O_TAPS + 8 * TROW;
+    static constexpr int O_WSPL = 0;
+    static constexpr int O_XF = O_WSPL + 16 * WROW;
     static constexpr int O_TB = O_XF + 2 * PRE * XBLK;
     static constexpr int O_XS = O_TB + 16 * TT;
     static constexpr int O_PART = O_XS + (2 * XS + 3) / 4 * 4;
-    static constexpr int O_ZE = O_PART + NPW * PROW;
-    static constexpr int WORDS = O_ZE + 3 * SA;
-    static_assert(NA % R == 0 && K % NP == 0 && SA % 8 == 0 && R == 8, "shapes");
-    static_assert(O_XF % 4 == 0 && O_TB % 4 == 0 && O_XS % 4 == 0 && O_PART % 4 == 0 && XROW % 4 == 0 &&
-                      S1STR % 4 == 0 && TT % 4 == 0 && TP % 4 == 0,
+    static constexpr int O_EZ = O_PART + 16 * PROW + 16;    // e z_o limb pairs [2][SA]
+    static constexpr int WORDS = O_EZ + 4 * SA;
+    static_assert(NA % R == 0 && K % NP == 0 && SA % 16 == 0 && R == 8 && GSYM % 2 == 0, "shapes");
+    static_assert(O_WSPL % 4 == 0 && O_XF % 4 == 0 && O_TB % 4 == 0 && O_XS % 4 == 0 && O_PART % 4 == 0 &&
+                      O_EZ % 4 == 0 && XROW % 4 == 0 && S1STR % 4 == 0 && TT % 4 == 0 && TP % 4 == 0 &&
+                      WROW % 4 == 0,
                   "16-byte aligned rows");
+    static constexpr int part_row(int task) { return task * PROW + (task >= 8 ? 16 : 0); }
 };
 
 __device__ __forceinline__ int32_t sx8s(uint32_t w, int sh) { return (int32_t)(w << (24 - sh)) >> 24; }
@@ -95,10 +102,29 @@ __device__ __forceinline__ void cp_async4s(uint32_t *smem, const uint32_t *gmem,
 
 __device__ __forceinline__ void cp_async_wait_alls() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-__device__ __forceinline__ int64_t mad_wides(int32_t a, int32_t b, int64_t c) {
-    int64_t d;
-    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-    return d;
+// a b (mod F) as a lazy residue (|result| < 2^17) for |a| < 2^18, |b| <= 2^15 + 8:
+// the 64-bit product is hi 2^32 + lo with 2^32 = 1 (mod F), and lo = l1 2^16 + l0
+// with 2^16 = -1, so a b = hi + l0 - l1 (mod F).
+__device__ __forceinline__ int32_t mulred(int32_t a, int32_t b) {
+    const int64_t t = (int64_t)a * b;
+    const uint32_t lo = (uint32_t)t;
+    return (int32_t)(t >> 32) + (int32_t)(lo & 0xFFFFu) - (int32_t)(lo >> 16);
+}
+
+// Byte J of w (J runtime), sign-extended.
+__device__ __forceinline__ int32_t sbyte_rt(uint32_t w, uint32_t sel) {
+    int32_t r;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(w), "r"(sel));
+    return r;
+}
+
+// Byte j of w, sign-extended (prmt with the sign-replicating selector nibbles).
+template <int J>
+__device__ __forceinline__ int32_t sbyte(uint32_t w) {
+    constexpr uint32_t sel = J | ((8 | J) << 4) | ((8 | J) << 8) | ((8 | J) << 12);
+    int32_t r;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(w), "r"(sel));
+    return r;
 }
 
 // Named barriers: 1 = the consumer warps, 2 = every warp of the CTA.
@@ -148,22 +174,19 @@ __device__ __forceinline__ void produce(const AeqChain &ch, const uint32_t *xin,
     StoreSpectrum<C, 0>::run(v, xf + b * C::XBLK + s1 * C::S1STR);
 }
 
-// Decoded, weighted outputs of the kept groups m >= MKEEP (register i of the
-// R-point stage holds group m = bitrev_R(i)) of output column n' = q, summed
-// over the warp's tasks and stored by the first task's threads at block
-// position n' + NP m - K.
+// Kept outputs m >= MKEEP (register i of the R-point stage holds group
+// m = bitrev_R(i)) of output column n' = q, stored at block position
+// n' + NP m - K of the task's row (threads r < NP of the task, one per column).
+// A per-pair convolution value c has |c| <= 32512 (constraint (5)) and the
+// register holds c + jF with |c + jF| < 2^18; the centred reduction rhoc then
+// returns c itself (its result lies within 2^15 + 5 of zero, and c is the only
+// representative there), so no further fix-up is needed.
 template <class C, int I>
-struct KeepOutputs {
-    static __device__ __forceinline__ void run(const int32_t (&a)[C::R], int32_t wgt, int32_t *prow, int q,
-                                               int lane) {
+struct StoreOutputs {
+    static __device__ __forceinline__ void run(const int32_t (&a)[C::R], int32_t *prow, int q) {
         constexpr int m = bitrev(I, ilog2(C::R));
-        if constexpr (m >= C::MKEEP) {
-            int32_t v = decode(a[I]) * wgt;
-#pragma unroll
-            for (int s = C::R; s < 32; s <<= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
-            if (lane < C::NP) prow[q + C::NP * m - C::K] = v;   // the warp's first task, one thread per n'
-        }
-        if constexpr (I + 1 < C::R) KeepOutputs<C, I + 1>::run(a, wgt, prow, q, lane);
+        if constexpr (m >= C::MKEEP) prow[q + C::NP * m - C::K] = rhoc(a[I]);
+        if constexpr (I + 1 < C::R) StoreOutputs<C, I + 1>::run(a, prow, q);
     }
 };
 
@@ -174,13 +197,12 @@ __global__ void __launch_bounds__(SerCfg<NA, ALPHA>::NTHR, 1)
     using C = SerCfg<NA, ALPHA>;
     constexpr int K = C::K, SA = C::SA, R = C::R, NP = C::NP;
     extern __shared__ __align__(16) uint32_t smem[];
-    int32_t *ttab = (int32_t *)smem + C::O_TAPS;
+    int32_t *wspl = (int32_t *)smem + C::O_WSPL;     // tap groups [filter][g][WROW]: T >> 23, (T >> 16) & 127
     int32_t *xf2 = (int32_t *)smem + C::O_XF;
     int32_t *tb = (int32_t *)smem + C::O_TB;
     uint32_t *xs2 = smem + C::O_XS;
     int32_t *part = (int32_t *)smem + C::O_PART;
-    int32_t *zs = (int32_t *)smem + C::O_ZE;     // z of both outputs [2][SA], then e [SA]
-    int32_t *es = zs + 2 * SA;
+    int2 *ez2 = (int2 *)(smem + C::O_EZ);             // e z_o as limbs (c0, c1) [o][SA]
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -213,12 +235,29 @@ __global__ void __launch_bounds__(SerCfg<NA, ALPHA>::NTHR, 1)
             pw = pw * ai % kF;
         }
     }
-    // phase-3 role: filter f = warp (o = f >> 2, s1 = f & 3), taps k0 .. k0 + 3,
-    // symbols i0 .. i0 + GSYM - 1
-    const int gf = warp & 7, go = gf >> 2, gs1 = gf & 3;
-    const int gsp = lane & 7, k0 = 4 * ((lane >> 3) & 3), i0 = gsp * C::GSYM;
+    // phase-3 role (C::G4 layout or the N = 32 one).  The lane that ends up
+    // with the sum of filter (go, gs1), tap gk owns that master tap: it keeps T
+    // in a register, updates it and publishes its two 7-bit groups.
+    int go, gk, gsp, gs1;
+    bool owner;
+    if constexpr (C::G4) {
+        go = (warp >> 2) & 1;
+        gk = 4 * (warp & 3) + ((lane >> 3) & 3);
+        gsp = lane & 7;
+        gs1 = 2 * ((gsp >> 2) & 1) + ((gsp >> 1) & 1);
+        owner = !producer && (lane & 1) == 0;
+    } else {
+        gsp = tid & 1;
+        gs1 = (tid >> 1) & 3;
+        gk = (tid >> 3) & 15;
+        go = (tid >> 7) & 1;
+        owner = !producer && gsp == 0;
+    }
+    const int i0 = gsp * C::GSYM;
     const int gb1 = (gsp >> 1) & 1, gb2 = (gsp >> 2) & 1;
-    const int gk = k0 + 2 * gb2 + gb1;             // the tap this lane holds after the reduction
+    const int gf = 4 * go + gs1;
+    const uint32_t gsel = 0x8880u + 0x1111u * (uint32_t)gs1;   // prmt: byte gs1, sign-extended
+    int32_t treg = 0;
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const AeqChain ch = chains[item >> 1];
@@ -229,14 +268,15 @@ __global__ void __launch_bounds__(SerCfg<NA, ALPHA>::NTHR, 1)
         const int64_t nblk = (ch.end - ch.begin + SA - 1) / SA;
         const int64_t nbatch = (nblk + C::PRE - 1) / C::PRE;
 
-        if (tid < 8 * K) {
-            const int f = tid >> 4, k = tid & 15;
-            ttab[f * C::TROW + k] = ch.init[((2 * p + (f >> 2)) * 4 + (f & 3)) * K + k];
+        if (owner) {
+            treg = ch.init[((2 * p + go) * 4 + gs1) * K + gk];
+            wspl[(2 * gf) * C::WROW + gk] = treg >> 23;
+            wspl[(2 * gf + 1) * C::WROW + gk] = (treg >> 16) & 127;
         }
         if (producer && nbatch > 0) produce<C>(ch, xin, 0, xs2, xf2, lane);
         bar_all(C::NTHR);
 
-        int64_t gsum = 0;                          // gradient of tap gk over the period
+        int64_t gsum = 0;                          // gradient of (go, gs1, gk) over the period
         int in_period = 0;
         for (int64_t j = 0; j < nbatch; ++j) {
             const int buf = (int)(j & 1);
@@ -253,17 +293,15 @@ __global__ void __launch_bounds__(SerCfg<NA, ALPHA>::NTHR, 1)
 
                     // ---- phase 1: tap transforms, products, inverses, outputs
                     if (tid < 16 * R) {
-                        const int32_t *trow = ttab + (4 * po + ps1) * C::TROW;
-                        const int tsh = pg ? 16 : 23;             // hi = T >> 23, lo = (T >> 16) & 127
-                        const int32_t tmask = pg ? 127 : -1;
+                        const int32_t *wrow = wspl + (2 * (4 * po + ps1) + pg) * C::WROW;
                         int32_t w[K];
 #pragma unroll
                         for (int q = 0; q < K / 4; ++q) {
-                            const int4 t4 = *(const int4 *)(trow + 4 * q);
-                            w[4 * q] = (t4.x >> tsh) & tmask;
-                            w[4 * q + 1] = (t4.y >> tsh) & tmask;
-                            w[4 * q + 2] = (t4.z >> tsh) & tmask;
-                            w[4 * q + 3] = (t4.w >> tsh) & tmask;
+                            const int4 t4 = *(const int4 *)(wrow + 4 * q);
+                            w[4 * q] = t4.x;
+                            w[4 * q + 1] = t4.y;
+                            w[4 * q + 2] = t4.z;
+                            w[4 * q + 3] = t4.w;
                         }
                         int32_t u[NP];
 #pragma unroll
@@ -278,16 +316,16 @@ __global__ void __launch_bounds__(SerCfg<NA, ALPHA>::NTHR, 1)
 #pragma unroll
                         for (int i = 0; i < NP; i += 4) {
                             const int4 x4 = *(const int4 *)(xrow + i);
-                            u[i] = rho(rhoc(u[i]) * x4.x);
-                            u[i + 1] = rho(rhoc(u[i + 1]) * x4.y);
-                            u[i + 2] = rho(rhoc(u[i + 2]) * x4.z);
-                            u[i + 3] = rho(rhoc(u[i + 3]) * x4.w);
+                            u[i] = mulred(u[i], x4.x);
+                            u[i + 1] = mulred(u[i + 1], x4.y);
+                            u[i + 2] = mulred(u[i + 2], x4.z);
+                            u[i + 3] = mulred(u[i + 3], x4.w);
                         }
                         fnt_inv<NP, C::BETA, 17>(u);
                         int32_t *trows = tb + task * C::TT;
                         trows[r] = rho(u[0]);
 #pragma unroll
-                        for (int n = 1; n < NP; ++n) trows[n * C::TP + r] = rho(rhoc(u[n]) * twi[n]);
+                        for (int n = 1; n < NP; ++n) trows[n * C::TP + r] = mulred(u[n], twi[n]);
                         __syncwarp();
                         // after the transpose thread r takes output column n' = r mod NP
                         // (when NP < R, threads r and r + NP compute the same column)
@@ -302,69 +340,88 @@ __global__ void __launch_bounds__(SerCfg<NA, ALPHA>::NTHR, 1)
                             a[q + 3] = v4.w;
                         }
                         fnt_fwd<R, C::GAMMA, 17>(a);
-                        KeepOutputs<C, 0>::run(a, pg ? 1 : 128, part + warp * C::PROW, nq, lane);
+                        if (r < NP) StoreOutputs<C, 0>::run(a, part + C::part_row(task), nq);
                     }
                     bar_consumers(C::NCONS);
 
-                    // ---- phase 2: outputs and RDE error of the polarisation
-                    if (tid < SA) {
-                        const int i = tid;
-                        int32_t y0 = 0, y1 = 0;
+                    // ---- phase 2: outputs and RDE error; thread (symbol i, output o)
+                    if (tid < 2 * SA) {
+                        const int i = tid >> 1, o = tid & 1;
+                        const int32_t *pc = part + C::part_row(8 * o) + i;
+                        int32_t y = 0;              // sum over s1 of 128 c_hi + c_lo (tasks 2 s1 + g)
 #pragma unroll
-                        for (int w = 0; w < C::NPW / 2; ++w) {
-                            y0 += part[w * C::PROW + i];
-                            y1 += part[(C::NPW / 2 + w) * C::PROW + i];
-                        }
-                        const int32_t z0 = min(max(y0 >> 7, -32768), 32767);
-                        const int32_t z1 = min(max(y1 >> 7, -32768), 32767);
+                        for (int t = 0; t < 8; t += 2) y += 128 * pc[t * C::PROW] + pc[(t + 1) * C::PROW];
+                        const int32_t z = min(max(y >> 7, -32768), 32767);
+                        const int32_t zp = __shfl_xor_sync(0xffffffffu, z, 1);
+                        const int32_t z0 = o ? zp : z, z1 = o ? z : zp;
                         const int64_t t = t0 + i;
                         const bool valid = t < ch.end;
                         const int64_t r2 = (int64_t)z0 * z0 + (int64_t)z1 * z1;
                         const int64_t Rr = r2 < 6 * A2 ? 2 * A2 : (r2 < 14 * A2 ? 10 * A2 : 18 * A2);
-                        if (valid && t >= ch.keep)
+                        if (o == 0 && valid && t >= ch.keep)
                             *(uint32_t *)(out + t * 4 + 2 * p) = ((uint32_t)z0 & 0xFFFFu) | ((uint32_t)z1 << 16);
-                        zs[i] = valid ? z0 : 0;
-                        zs[SA + i] = valid ? z1 : 0;
-                        es[i] = valid ? (int32_t)(Rr - r2) : 0;
+                        // e z_o (|e z| <= 2^31 2^15 = 2^46) as a 23-bit low limb and the
+                        // signed rest: e z = c1 2^23 + c0, 0 <= c0 < 2^23, |c1| <= 2^23
+                        const int64_t ez = valid ? (int64_t)(int32_t)(Rr - r2) * z : 0;
+                        ez2[o * SA + i] = make_int2((int32_t)(ez & 0x7FFFFF), (int32_t)(ez >> 23));
                     }
                     bar_consumers(C::NCONS);
 
                     // ---- phase 3: gradient of eq. (6) and the tap update
                     if (mu < 63) {
-                        const int8_t *xb = (const int8_t *)(xs + bb * SA + K - k0) + gs1;   // x_s1[t0 + i - k0] at xb[4 i]
-                        int32_t w1 = xb[4 * (i0 - 1)], w2 = xb[4 * (i0 - 2)], w3 = xb[4 * (i0 - 3)];
-                        const int32_t *zrow = zs + go * SA;
-                        int64_t acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+                        // word of symbol t0 + i - k (all four inputs) at xw[i]
+                        const uint32_t *xw = xs + bb * SA + K - gk;
+                        const int2 *ez = ez2 + go * SA + i0;
+                        int64_t kv;
+                        // G = sum_i (c1_i 2^23 + c0_i) x_i: each limb sum over a thread's
+                        // GSYM <= 8 symbols stays below 8 2^23 16 = 2^30, exact in int32
+                        if constexpr (C::G4) {
+                            int32_t l0[4] = {0, 0, 0, 0}, l1[4] = {0, 0, 0, 0};
 #pragma unroll
-                        for (int ii = 0; ii < C::GSYM; ++ii) {
-                            const int i = i0 + ii;
-                            const int32_t w0 = xb[4 * i];
-                            const int32_t e = es[i], z = zrow[i];
-                            acc0 = mad_wides(e, z * w0, acc0);          // |z x| <= 2^19
-                            acc1 = mad_wides(e, z * w1, acc1);
-                            acc2 = mad_wides(e, z * w2, acc2);
-                            acc3 = mad_wides(e, z * w3, acc3);
-                            w3 = w2;
-                            w2 = w1;
-                            w1 = w0;
+                            for (int ii = 0; ii < C::GSYM; ii += 2) {
+                                const int4 q = *(const int4 *)(ez + ii);     // limbs of symbols i, i + 1
+                                const uint32_t wa = xw[i0 + ii], wb = xw[i0 + ii + 1];
+                                const int32_t xa[4] = {sbyte<0>(wa), sbyte<1>(wa), sbyte<2>(wa), sbyte<3>(wa)};
+                                const int32_t xb[4] = {sbyte<0>(wb), sbyte<1>(wb), sbyte<2>(wb), sbyte<3>(wb)};
+#pragma unroll
+                                for (int s = 0; s < 4; ++s) {
+                                    l0[s] += q.x * xa[s] + q.z * xb[s];
+                                    l1[s] += q.y * xa[s] + q.w * xb[s];
+                                }
+                            }
+                            int64_t acc[4];
+#pragma unroll
+                            for (int s = 0; s < 4; ++s) acc[s] = ((int64_t)l1[s] << 23) + l0[s];
+                            // sum over the 8 symbol ranges (lane bits 0..2); the lane
+                            // keeps input s1 = 2 b2 + b1
+                            int64_t k01 = gb2 ? acc[2] : acc[0], k11 = gb2 ? acc[3] : acc[1];
+                            const int64_t s01 = gb2 ? acc[0] : acc[2], s11 = gb2 ? acc[1] : acc[3];
+                            k01 += __shfl_xor_sync(0xffffffffu, s01, 4);
+                            k11 += __shfl_xor_sync(0xffffffffu, s11, 4);
+                            kv = gb1 ? k11 : k01;
+                            kv += __shfl_xor_sync(0xffffffffu, gb1 ? k01 : k11, 2);
+                            kv += __shfl_xor_sync(0xffffffffu, kv, 1);
+                        } else {
+                            int32_t l0 = 0, l1 = 0;
+#pragma unroll
+                            for (int ii = 0; ii < C::GSYM; ii += 2) {
+                                const int4 q = *(const int4 *)(ez + ii);
+                                const int32_t xa = sbyte_rt(xw[i0 + ii], gsel), xb = sbyte_rt(xw[i0 + ii + 1], gsel);
+                                l0 += q.x * xa + q.z * xb;
+                                l1 += q.y * xa + q.w * xb;
+                            }
+                            kv = ((int64_t)l1 << 23) + l0;
+                            kv += __shfl_xor_sync(0xffffffffu, kv, 1);    // the two symbol halves
                         }
-                        // sum over the 8 symbol ranges (lane bits 0..2); the lane
-                        // keeps tap k0 + 2 b2 + b1
-                        int64_t k01 = gb2 ? acc2 : acc0, k11 = gb2 ? acc3 : acc1;
-                        const int64_t s01 = gb2 ? acc0 : acc2, s11 = gb2 ? acc1 : acc3;
-                        k01 += __shfl_xor_sync(0xffffffffu, s01, 4);
-                        k11 += __shfl_xor_sync(0xffffffffu, s11, 4);
-                        int64_t kv = gb1 ? k11 : k01;
-                        kv += __shfl_xor_sync(0xffffffffu, gb1 ? k01 : k11, 2);
-                        kv += __shfl_xor_sync(0xffffffffu, kv, 1);
                         gsum += kv;
                         if (++in_period == period || blk + 1 == nblk) {
                             in_period = 0;
-                            if ((lane & 1) == 0) {
-                                int32_t *tp = ttab + gf * C::TROW + gk;
-                                int64_t v = (int64_t)*tp + (gsum >> mu);
+                            if (owner) {
+                                int64_t v = (int64_t)treg + (gsum >> mu);
                                 v = v < -(1ll << 29) ? -(1ll << 29) : (v > (1ll << 29) - 1 ? (1ll << 29) - 1 : v);
-                                *tp = (int32_t)v;
+                                treg = (int32_t)v;
+                                wspl[(2 * gf) * C::WROW + gk] = treg >> 23;
+                                wspl[(2 * gf + 1) * C::WROW + gk] = (treg >> 16) & 127;
                             }
                             gsum = 0;
                         }
@@ -374,10 +431,7 @@ __global__ void __launch_bounds__(SerCfg<NA, ALPHA>::NTHR, 1)
             }
             bar_all(C::NTHR);
         }
-        if (ch.write_state && tid < 8 * K) {
-            const int f = tid >> 4, k = tid & 15;
-            fr.state[((2 * p + (f >> 2)) * 4 + (f & 3)) * K + k] = ttab[f * C::TROW + k];
-        }
+        if (ch.write_state && owner) fr.state[((2 * p + go) * 4 + gs1) * K + gk] = treg;
         bar_all(C::NTHR);
     }
 }
