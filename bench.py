@@ -5,16 +5,16 @@ One step = one pass of the whole hot path (FNT-CDC on both polarisations,
 requantise + resample, FNT-AEQ with RDE adaptation) over one batch of synthetic
 input already resident in device memory.  Default workload: one PDM-16QAM
 stream, 40 GBaud at 2 samples/symbol, 2^20 symbols per polarisation, 75 km
-(17 CD taps, 6 bit), 5-bit I/Q, AEQ 4x4 RV-MIMO at N = 64 / radix 4080 in
-segments of 864 symbols (18 AEQ blocks) that read the 16 preceding symbols of
-the stream as input history, every segment starting from
-the tap state the previous step ended with (a stream processed step by step).
+(17 CD taps, 6 bit), 5-bit I/Q, AEQ 4x4 RV-MIMO at N = 64 / radix 4080 with the
+RDE update of eq. (6) after every block over the whole stream (one serial
+recurrence per polarisation), every step continuing from the tap state the
+previous step ended with (a stream processed step by step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fnt|reference]
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
-host cores instead (bounded sample of the same workload).  With N > 1 (launched
-by torch.distributed.run) every rank runs an independent replica on its own GPU
+host (bounded sample of the same workload).  With N > 1 (launched by
+torch.distributed.run) every rank runs an independent replica on its own GPU
 (the path has no exchange step); value = all ranks' samples / max rank time.
 """
 from __future__ import annotations
@@ -42,16 +42,21 @@ UNIT = "Gsamples/s"
 # ---------------------------------------------------------------- workload ----
 
 WORKLOADS = {
-    "cfg2": dict(n_sym=1 << 20, km=75.0, n_aeq=64, alpha_aeq=4080, segment=864, warmup=0,
+    "cfg2": dict(n_sym=1 << 20, km=75.0, n_aeq=64, alpha_aeq=4080, segment=0, warmup=0,
                  desc="PDM-16QAM 40 GBaud 2 sps, 2^20 symbols/pol (2^21 samples), 75 km, 17 CD taps (6 bit), "
-                      "5-bit I/Q, FNT-CDC N=64 alpha=4080 S=48 + FNT-AEQ 4x4 RV-MIMO N=64 alpha=4080 K=16, "
-                      "AEQ segments of 864 symbols (18 blocks) starting from the stream's carried taps, each "
-                      "reading the 16 preceding symbols of the stream as input history"),
+                      "5-bit I/Q, FNT-CDC N=64 alpha=4080 S=48 + FNT-AEQ 4x4 RV-MIMO N=64 alpha=4080 K=16 with the "
+                      "RDE update of eq. (6) after every block over the whole stream (one serial recurrence per "
+                      "polarisation, 21846 blocks), continuing from the stream's carried taps"),
     "cfg5": dict(n_sym=1 << 26, km=80.0, n_aeq=32, alpha_aeq=2, segment=1 << 16, warmup=1 << 12,
                  desc="PDM bandwidth stress, one stream of 2^27 samples/pol (a generated 2^23-sample stretch "
                       "repeated), 80 km, 19 CD taps, FNT-AEQ N=32 alpha=2, segments 2^16 + 2^12 warm-up from "
                       "the carried taps"),
 }
+# Other AEQ semantics reported beside the cfg-2 headline (extra keys, not the
+# headline): the segment rule fixed in advance for long streams (2^16-symbol
+# segments each starting 2^12 symbols early), and 864-symbol segments without
+# warm-up (a length chosen for throughput on this GPU).  Both change the outputs.
+CFG2_OTHER = {"segments_65536_warmup_4096": (1 << 16, 1 << 12), "segments_864_no_warmup": (864, 0)}
 MU_SHIFT = 9
 L2_BYTES = 129 << 20                     # GB300 L2
 TAP_INIT = 2048
@@ -109,10 +114,26 @@ def profiled_traffic(kernel: str, src_hash: str):
     return rec.get("dram_bytes_per_launch")
 
 
+def profiled_counters(kernel: str, src_hash: str):
+    """Issue and pipe utilisation of the kernel from the committed ncu summary
+    (same source hash only), for comparison with the bench's own fraction."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_hash") != src_hash:
+        return None
+    keys = ("issue_active_pct", "alu_pipe_pct", "fma_pipe_pct", "warp_instructions_per_launch", "workload")
+    out = {k: rec[k] for k in keys if k in rec}
+    return out or None
+
+
 # ------------------------------------------------------------------ clocks ----
 
 class ClockSampler:
-    """nvidia-smi samples (100 ms) while the timed region runs."""
+    """nvidia-smi samples (every 10 ms) while the timed region runs."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -126,7 +147,7 @@ class ClockSampler:
             return
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", gpu_id], stdout=subprocess.PIPE,
+                                          "-lms", "10", "-i", gpu_id], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -236,7 +257,21 @@ def _segments(x_np, taps, wl, n_seg):
 
 # ---------------------------------------------------------------- main arm ----
 
-def run_fnt(args, rank, world, local_rank):
+def _oracle_full_step(x, taps, prm_kw, T0):
+    """Spawned worker: the oracle over the whole step from T0 (CDC, requantise,
+    resample, then the AEQ recurrence), timed; returns (seconds, output)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    out, _ = oracle.chain(x, taps, oracle.ChainParams(**prm_kw), T0=T0)
+    return time.perf_counter() - t0, out
+
+
+def _bounded_steps(ms_per_step: float, seconds: float, lo: int = 3, hi: int = 200) -> int:
+    return int(max(lo, min(hi, seconds * 1e3 / max(ms_per_step, 1e-3))))
+
+
+def run_fnt(args, rank, world, local_rank, oracle_pool=None):
     import torch
     import paper_2405_04253_gb300 as fnt
     import synth
@@ -249,10 +284,15 @@ def run_fnt(args, rank, world, local_rank):
     n = x_np.shape[0]
     L = taps.shape[0]
     S = 64 - L + 1
-    plan = fnt.Plan(n_aeq=wl["n_aeq"], alpha_aeq=wl["alpha_aeq"], mu_shift=MU_SHIFT,
-                    aeq_segment=wl["segment"], aeq_warmup=wl["warmup"], aeq_update_period=wl.get("period", 1),
-                    aeq_freq_sum=wl.get("freq_sum", 0))
-    plan.set_tensor_gradient(args.tensor_gradient)
+    serial = wl["segment"] == 0
+
+    def make_plan(segment, warmup):
+        p = fnt.Plan(n_aeq=wl["n_aeq"], alpha_aeq=wl["alpha_aeq"], mu_shift=MU_SHIFT, aeq_segment=segment,
+                     aeq_warmup=warmup, aeq_update_period=wl.get("period", 1), aeq_freq_sum=wl.get("freq_sum", 0))
+        p.set_tensor_gradient(args.tensor_gradient)
+        return p
+
+    plan = make_plan(wl["segment"], wl["warmup"])
     nsym = fnt.chain_nsym(n, L)
     # The stream's batches rotate over a ring of device buffers whose inputs
     # together exceed twice the 129 MB L2, so every step reads an input that is
@@ -262,8 +302,7 @@ def run_fnt(args, rank, world, local_rank):
     x0 = torch.from_numpy(x_np).to(dev)
     xs = [x0] + [x0.clone() for _ in range(ring - 1)]
     outs = [torch.zeros((nsym, 4), dtype=torch.int16, device=dev) for _ in range(ring)]
-    state = torch.zeros((4, 4, 16), dtype=torch.int32, device=dev)       # the stream's carried AEQ taps
-    state[[0, 1, 2, 3], [0, 1, 2, 3], 8] = TAP_INIT << 16
+    state = torch.from_numpy(init_taps()).to(dev)          # the stream's carried AEQ taps
     # a step: one slot's prepared CDC + AEQ launches replayed as one CUDA graph
     batches = [fnt.Batch(plan, [fnt.Frame(xs[r], outs[r], taps, state)], fnt.OP_CHAIN, use_graph=True)
                for r in range(ring)]
@@ -281,7 +320,15 @@ def run_fnt(args, rank, world, local_rank):
         b.launch_stage(1, stream)
         evs[2].record(stream)
 
-    for r in range(ring):                 # records every slot's graph
+    # the first step runs from the plan's initial taps: the oracle recomputes it
+    # (in a spawned process, while the GPU is timed)
+    step(0)
+    torch.cuda.synchronize()
+    out_first = outs[0].cpu().numpy().copy()
+    oracle_job = None
+    if oracle_pool is not None:
+        oracle_job = oracle_pool.apply_async(_oracle_full_step, (x_np, taps, _prm_kw(wl), init_taps()))
+    for r in range(1, ring):              # records every slot's graph
         step(r)
     for k in range(args.warmup):
         step(k)
@@ -299,10 +346,6 @@ def run_fnt(args, rank, world, local_rank):
         gpu_id = str(local_rank)
     clocks = ClockSampler(gpu_id if rank == 0 else None)
     time.sleep(0.3)
-    k2 = min(args.steps, 200)
-    evs2 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(k2)]
-    for k in range(3):
-        step_staged(k, evs2[0])
     t_beg, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
@@ -314,7 +357,14 @@ def run_fnt(args, rank, world, local_rank):
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     barrier()
-    # per-kernel durations: the same steps as two plain launches, events around each
+    clk = clocks.stop()
+    total_ms = reduce_max(t_beg.elapsed_time(t_end), dev)
+    ms_per_step = total_ms / args.steps
+    value = aggregate(n, world, ms_per_step * 1e-3)
+    # per-kernel durations: the same steps as two plain launches, events around
+    # each (about two seconds of steps)
+    k2 = _bounded_steps(ms_per_step, 2.0)
+    evs2 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(k2)]
     for k in range(k2):
         step_staged(k, evs2[k])
     torch.cuda.synchronize()
@@ -329,20 +379,51 @@ def run_fnt(args, rank, world, local_rank):
         evr[j][1].record(stream)
     torch.cuda.synchronize()
     rep_ms = sorted(e[0].elapsed_time(e[1]) / rep_steps for e in evr)
-    clk = clocks.stop()
     cdc_ms = [e[0].elapsed_time(e[1]) for e in evs2]
     aeq_ms = [e[1].elapsed_time(e[2]) for e in evs2]
     staged_ms = statistics.mean(e[0].elapsed_time(e[2]) for e in evs2)
-    total_ms = reduce_max(t_beg.elapsed_time(t_end), dev)
-    ms_per_step = total_ms / args.steps
-    value = aggregate(n, world, ms_per_step * 1e-3)
 
-    # one more step from a recorded tap state: its output is what the CPU-baseline
-    # leg recomputes
+    # one more step from a recorded tap state: the end-to-end leg repeats it
     state_snap = state.cpu().numpy().copy()
     step(0)
     torch.cuda.synchronize()
     out_check = outs[0].clone()
+
+    # other AEQ semantics on the same stream (extra keys; their outputs differ
+    # from the headline's): each from its own carried state, same rotation
+    other = {}
+    if args.workload == "cfg2" and serial and not args.no_other_semantics:
+        for name, (seg, warm) in CFG2_OTHER.items():
+            p_o = make_plan(seg, warm)
+            st_o = torch.from_numpy(init_taps()).to(dev)
+            o_o = [torch.zeros((nsym, 4), dtype=torch.int16, device=dev) for _ in range(2)]
+            b_o = [fnt.Batch(p_o, [fnt.Frame(xs[r], o_o[r % 2], taps, st_o)], fnt.OP_CHAIN, use_graph=True)
+                   for r in range(ring)]
+            for r in range(ring):
+                b_o[r].launch(stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(5):
+                b_o[k % ring].launch(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            k_o = _bounded_steps(e0.elapsed_time(e1) / 5, 1.0, 10, 5000)
+            e0.record(stream)
+            for k in range(k_o):
+                b_o[k % ring].launch(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_o = reduce_max(e0.elapsed_time(e1), dev) / k_o
+            n_chains = math.ceil(nsym / seg)
+            other[name] = {"value": round(aggregate(n, world, ms_o * 1e-3), 4), "ms_per_step": round(ms_o, 4),
+                           "steps": k_o, "aeq_segment": seg, "aeq_warmup": warm, "aeq_chains": n_chains,
+                           "semantics": f"each {seg}-symbol output segment re-runs the AEQ from the taps the stream "
+                                        f"carried into the step, starting {warm} symbols early and reading the 16 "
+                                        "stream symbols before its start as history; outputs differ from the "
+                                        "headline's recurrence over the whole stream"}
+            for b_ in b_o:
+                b_.close()
 
     # End to end through the public API with the stream's samples in page-locked
     # host memory: a prepared batch per host buffer (fnt_batch_create with
@@ -422,24 +503,47 @@ def run_fnt(args, rank, world, local_rank):
     dom = "aeq" if aeq_avg >= cdc_avg else "cdc"
     ops = aeq_ops(nsym, wl["n_aeq"]) if dom == "aeq" else cdc_ops(n, S)
     dur = aeq_avg if dom == "aeq" else cdc_avg
-    kname = f"aeq_kernel<{wl['n_aeq']}>" if dom == "aeq" else "cdc_kernel<chain>"
-    src = source_hash("aeq.cu", "zf.cuh", "internal.h") if dom == "aeq" else source_hash("cdc.cu", "zf.cuh",
-                                                                                      "internal.h")
+    n_items = 2 * (math.ceil(nsym / wl["segment"]) if wl["segment"] else 1)    # (chain, polarisation) pairs
+    aeq_cta = plan.aeq_kernel_for(n_items // 2) == 2
+    if dom == "aeq":
+        kname = f"aeq_serial_kernel<{wl['n_aeq']}>" if aeq_cta else f"aeq_kernel<{wl['n_aeq']}>"
+        src = source_hash("aeq_serial.cu" if aeq_cta else "aeq.cu", "zf.cuh", "internal.h")
+    else:
+        kname, src = "cdc_kernel<chain>", source_hash("cdc.cu", "zf.cuh", "internal.h")
     achieved = ops / (dur * 1e-3) / 1e12
     peak = alu_peak_ops() / 1e12
-    roof = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 3), "peak": round(peak, 2),
-            "unit": "Tops/s (int32, algorithmic)", "frac": round(achieved / peak, 4),
+    roof = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 4), "peak": round(peak, 2),
+            "unit": "Tops/s (int32, algorithmic)", "frac": round(achieved / peak, 5),
             "traffic": profiled_traffic(kname, src), "avg_launch_ms": round(dur, 4),
-            "peak_basis": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (issue-bound int32)"}
+            "peak_basis": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (issue-bound int32), derived"}
+    prof = profiled_counters(kname, src)
+    if prof:
+        roof["ncu"] = prof
+    if dom == "aeq" and aeq_cta:
+        # a (chain, polarisation) is one serial recurrence and one CTA: the
+        # launch can occupy at most n_items SMs
+        occ_peak = min(n_items, 152) * 4 * 32 * 2070e6 / 1e12
+        roof["occupied"] = {"sms": min(n_items, 152), "peak": round(occ_peak, 3),
+                            "frac": round(achieved / occ_peak, 4),
+                            "note": "the eq. (6) recurrence of each polarisation is serial over the stream's "
+                                    "blocks, so one stream occupies two SMs; frac here is against their issue bound"}
     hbm_bytes = n * 4 + nsym * 8
     res = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload + ": " + wl["desc"], "aeq_update_period": wl.get("period", 1),
+        "config": {"workload": args.workload + ": " + (wl["desc"] if serial or args.workload != "cfg2" else
+                                                       wl["desc"].split(" with the RDE")[0] +
+                                                       f" with the RDE update of eq. (6) in AEQ segments of "
+                                                       f"{wl['segment']} symbols + {wl['warmup']} warm-up from the "
+                                                       "stream's carried taps (not the recurrence over the whole "
+                                                       "stream)"),
+                   "aeq_segment": wl["segment"],
+                   "aeq_warmup": wl["warmup"], "aeq_update_period": wl.get("period", 1),
                    "aeq_freq_sum": wl.get("freq_sum", 0),
-                   "aeq_gradient": "tensor cores (exact f16 limbs, opt-in)" if args.tensor_gradient
-                   else "integer pipes (int64 multiply-add)",
+                   "aeq_kernel": "a CTA per (chain, polarisation)" if aeq_cta else "a warp per (chain, polarisation)",
+                   "aeq_gradient": "tensor cores (exact f16 limbs, opt-in)" if args.tensor_gradient and not aeq_cta
+                   else "integer pipes",
                    "samples_per_step": n, "symbols_per_step": nsym,
                    "l2": f"inputs rotate over {ring} device buffers of {x_np.nbytes >> 20} MiB "
                          f"({ring * x_np.nbytes >> 20} MiB > 2x the 129 MB L2), no flush",
@@ -455,15 +559,25 @@ def run_fnt(args, rank, world, local_rank):
                    "median_ms_per_step": round(statistics.median(rep_ms), 4),
                    "best_value": round(aggregate(n, world, rep_ms[0] * 1e-3), 4),
                    "median_value": round(aggregate(n, world, statistics.median(rep_ms) * 1e-3), 4)},
-        "hbm": {"achieved_gbs": round(hbm_bytes / (ms_per_step * 1e-3) / 1e9, 2), "peak_gbs": 6795.1,
-                "frac": round(hbm_bytes / (ms_per_step * 1e-3) / 1e9 / 6795.1, 5),
-                "bytes_per_step": hbm_bytes, "note": "algorithmic: int8 input + int16 output"},
+        "hbm": {"achieved_gbs": round(hbm_bytes / (ms_per_step * 1e-3) / 1e9, 3), "peak_gbs": 6782.1,
+                "frac": round(hbm_bytes / (ms_per_step * 1e-3) / 1e9 / 6782.1, 6),
+                "bytes_per_step": hbm_bytes, "note": "algorithmic: int8 input + int16 output; peak measured"},
         "gpu_launches": args.steps * batches[0].kernel_count(),
         "step": f"CUDA graph of {batches[0].kernel_count()} kernels (CDC, then AEQ) on the caller's stream",
         "clocks": clk,
         "wall_s_timed_region": round(wall, 3),
         "e2e": e2e,
     }
+    if other:
+        res["other_aeq_semantics"] = other
+    if oracle_job is not None:
+        secs, ref = oracle_job.get()
+        res["cpu_baseline"] = {"value": round(n / secs / 1e9, 7), "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"the whole first step ({n} samples) from the plan's initial taps: plain C "
+                                         "oracle (O(N^2) transforms), CDC then the AEQ recurrence, one process "
+                                         "(the recurrence is serial)" if serial else
+                                         f"the whole first step ({n} samples), one process",
+                               "seconds": round(secs, 2), "step_bitexact": bool(np.array_equal(out_first, ref))}
     return res, (x_np, taps, out_check, wl, state_snap)
 
 
@@ -505,34 +619,54 @@ def cpu_baseline(x_np, taps, wl, out_dev=None, n_seg=96, procs=None, T0=None):
 
 
 def run_reference(args):
-    """The CPU oracle as the reference arm: each step a bounded sample of the
-    same workload (args.ref_segments AEQ segments) on the host cores."""
+    """The CPU oracle as the reference arm, each step a bounded sample of the
+    same workload on the host: with the AEQ recurrence over the whole stream,
+    the oracle's chain over the stream's first args.ref_samples samples from
+    the plan's initial taps (one process: the recurrence is serial); with AEQ
+    segments, args.ref_segments segments in a spawn pool over the host cores."""
     import synth
     wl = WORKLOADS[args.workload if args.workload in WORKLOADS else "cfg2"]
     frame = synth.config2(wl["n_sym"]) if args.workload == "cfg2" else synth.config5(2 * wl["n_sym"])
-    procs = min(os.cpu_count() or 1, 16)
-    segs, total = _segments(frame.x, frame.taps, wl, args.ref_segments)
-    pool = OraclePool(frame.x, frame.taps, _prm_kw(wl), procs, init_taps())
-    try:
+    if wl["segment"] == 0:
+        import oracle
+        oracle.build()
+        m = min(args.ref_samples, frame.x.shape[0])
+        xp = np.ascontiguousarray(frame.x[:m])
+        prm = oracle.ChainParams(**_prm_kw(wl))
         for _ in range(args.warmup):
-            pool.run(segs[:procs])
-        secs, samples = 0.0, 0
+            oracle.chain(xp, frame.taps, prm, T0=init_taps())
+        secs = 0.0
         for _ in range(args.steps):
-            s_, n_, _ = pool.run(segs)
-            secs += s_
-            samples += n_
-    finally:
-        pool.close()
+            t0 = time.perf_counter()
+            oracle.chain(xp, frame.taps, prm, T0=init_taps())
+            secs += time.perf_counter() - t0
+        samples, procs = m * args.steps, 1
+        sample = (f"the stream's first {m} samples per step from the plan's initial taps: plain C oracle (O(N^2) "
+                  "transforms), CDC then the AEQ recurrence, one process (the recurrence is serial)")
+    else:
+        procs = min(os.cpu_count() or 1, 16)
+        segs, total = _segments(frame.x, frame.taps, wl, args.ref_segments)
+        pool = OraclePool(frame.x, frame.taps, _prm_kw(wl), procs, init_taps())
+        try:
+            for _ in range(args.warmup):
+                pool.run(segs[:procs])
+            secs, samples = 0.0, 0
+            for _ in range(args.steps):
+                s_, n_, _ = pool.run(segs)
+                secs += s_
+                samples += n_
+        finally:
+            pool.close()
+        sample = f"{len(segs)} of {total} AEQ segments per step, plain C oracle (O(N^2) transforms), spawn pool"
     value = samples / secs / 1e9
-    sample = f"{len(segs)} of {total} AEQ segments per step, plain C oracle (O(N^2) transforms), spawn pool"
-    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 1,
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 7), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
             "config": {"workload": args.workload + ": " + wl["desc"], "samples_per_step": samples // args.steps},
-            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": procs, "kind": "oracle",
+            "cpu_baseline": {"value": round(value, 7), "unit": UNIT, "cores": procs, "kind": "oracle",
                              "sample": sample},
-            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": round(value, 7), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 # ------------------------------------------------------- other workloads ----
@@ -738,8 +872,8 @@ def run_cfg4(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["fnt", "reference"], default="fnt")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["cfg1", "cfg3", "cfg4"], default="cfg2")
     ap.add_argument("--frames", type=int, default=0, help="cfg3 / cfg4: frame count (default 4096 / 2048)")
@@ -755,10 +889,23 @@ def main(argv=None):
                     help="cfg2 / cfg5: AEQ inputs summed in Z_F before the inverse transform (1 literal, 2 guarded)")
     ap.add_argument("--aeq-period", type=int, default=1,
                     help="cfg2 / cfg5: AEQ blocks per tap update (1 = every block, as in eq. (6))")
+    ap.add_argument("--aeq-segment", type=int, default=None,
+                    help="cfg2 / cfg5: AEQ segment length in symbols (0 = the recurrence over the whole stream; "
+                         "default: the workload's, 0 for cfg2); other values change the outputs")
+    ap.add_argument("--aeq-warmup", type=int, default=None, help="cfg2 / cfg5: AEQ segment warm-up in symbols")
+    ap.add_argument("--no-other-semantics", action="store_true",
+                    help="cfg2: skip the extra keys timed on segmented AEQ semantics")
+    ap.add_argument("--ref-samples", type=int, default=1 << 17,
+                    help="--impl reference, serial AEQ: stream prefix (samples) the oracle runs per step")
     args = ap.parse_args(argv)
     for wl in WORKLOADS.values():
         wl["period"] = args.aeq_period
         wl["freq_sum"] = args.aeq_freq_sum
+    if args.workload in WORKLOADS:
+        if args.aeq_segment is not None:
+            WORKLOADS[args.workload]["segment"] = args.aeq_segment
+        if args.aeq_warmup is not None:
+            WORKLOADS[args.workload]["warmup"] = args.aeq_warmup
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -785,8 +932,20 @@ def main(argv=None):
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    res, (x_np, taps, out, wl, T0) = run_fnt(args, rank, world, local_rank)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    wl = WORKLOADS[args.workload]
+    # the oracle's recomputation of the serial step runs in a process spawned
+    # before the GPU work, while the GPU is timed
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["segment"] == 0:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(1)
+    try:
+        res, (x_np, taps, out, wl, T0) = run_fnt(args, rank, world, local_rank, pool)
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and "cpu_baseline" not in res:
         res["cpu_baseline"] = cpu_baseline(x_np, taps, wl, out, n_seg=args.cpu_segments, T0=T0)
     if rank == 0:
         print(json.dumps(res), flush=True)

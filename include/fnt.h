@@ -317,6 +317,11 @@ FNT_API fnt_status fnt_plan_set_aeq_occupancy(fnt_plan *plan, int32_t max_warps_
  * not depend on it.  FNT_ERR_INVALID outside [0, 2]. */
 FNT_API fnt_status fnt_plan_set_aeq_kernel(fnt_plan *plan, int32_t kind);
 
+/* The AEQ kernel (1 or 2, as above) a launch of `n_chains` AEQ chains of this
+ * plan takes; 0 for a null plan.  A chain is a frame, or one AEQ segment of a
+ * frame. */
+FNT_API int32_t fnt_plan_aeq_kernel_for(const fnt_plan *plan, int64_t n_chains);
+
 /* The plan's initial AEQ taps (the state a frame without aeq_state, or a newly
  * configured serving link, starts from): HOST int32 [4 (S2)][4 (S1)][16],
  * zero except the centre tap of the four diagonal filters, tap_init << 16.

@@ -269,6 +269,11 @@ extern "C" fnt_status fnt_plan_set_aeq_kernel(fnt_plan *p, int32_t kind) {
     return FNT_OK;
 }
 
+extern "C" int32_t fnt_plan_aeq_kernel_for(const fnt_plan *p, int64_t n_chains) {
+    if (!p) return 0;
+    return aeq_use_serial(p, (int)std::min<int64_t>(n_chains, INT32_MAX)) ? 2 : 1;
+}
+
 // The CTA-per-chain kernel holds one (chain, polarisation) per SM: it is taken
 // when that many fit in one wave, and only for per-pair inverse transforms.
 bool fnt::aeq_use_serial(const fnt_plan *p, int n_chains) {

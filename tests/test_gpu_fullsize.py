@@ -59,3 +59,36 @@ def test_batch_of_4096_frames_sampled(orc):
     for i in sorted(pick):
         ref, _ = orc.chain(frames_np[i].x, frames_np[i].taps, orc.ChainParams(mu_shift=MU))
         assert np.array_equal(frames[i].out.cpu().numpy(), ref), i
+
+
+def test_cfg2_stream_serial_recurrence_whole_output(orc):
+    """The bench's headline workload in its launch configuration: the 2^21-
+    sample stream (2^20 symbols per polarisation, 17 taps, AEQ N = 64) as one
+    prepared graph batch with the AEQ unsegmented, so that eq. (6) updates the
+    taps after every one of the 21846 blocks of each polarisation's serial
+    recurrence (the CTA-per-chain kernel).  Every output symbol and the final
+    taps are compared with the oracle; a second launch continues from the
+    carried taps and is compared on its first and last blocks."""
+    f = synth.config2()
+    assert f.x.shape == (1 << 21, 2, 2) and f.taps.shape[0] == 17
+    kw = dict(n_aeq=64, alpha_aeq=4080, mu_shift=MU)
+    plan = F.Plan(**kw)
+    nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
+    assert plan.aeq_kernel_for(1) == 2
+    out = torch.full((nsym, 4), 0x4444, dtype=torch.int16, device="cuda")
+    T0 = orc.aeq_init_taps(16, 2048)
+    st = torch.from_numpy(T0).cuda()
+    b = F.Batch(plan, [F.Frame(torch.from_numpy(f.x).cuda(), out, f.taps, st)], F.OP_CHAIN, use_graph=True)
+    b.launch()
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    T1 = st.cpu().numpy()
+    ref, Tr = orc.chain(f.x, f.taps, orc.ChainParams(**kw), T0=T0)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(T1, Tr)
+    b.launch()
+    torch.cuda.synchronize()
+    got2 = out.cpu().numpy()
+    head, _ = orc.chain(f.x[: 48 * 2 * 40], f.taps, orc.ChainParams(**kw), T0=Tr)
+    assert np.array_equal(got2[: head.shape[0] - 24], head[: head.shape[0] - 24])
+    assert not np.array_equal(got2, got)
