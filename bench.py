@@ -298,7 +298,7 @@ def run_fnt(args, rank, world, local_rank, oracle_pool=None):
     # together exceed twice the 129 MB L2, so every step reads an input that is
     # not in L2 (no flush needed); all ring slots carry the same samples and
     # share the stream's tap state.
-    ring = max(1, math.ceil(2 * L2_BYTES / x_np.nbytes))
+    ring = max(1, min(64, math.ceil(2 * L2_BYTES / x_np.nbytes)))
     x0 = torch.from_numpy(x_np).to(dev)
     xs = [x0] + [x0.clone() for _ in range(ring - 1)]
     outs = [torch.zeros((nsym, 4), dtype=torch.int16, device=dev) for _ in range(ring)]
@@ -546,7 +546,9 @@ def run_fnt(args, rank, world, local_rank, oracle_pool=None):
                    else "integer pipes",
                    "samples_per_step": n, "symbols_per_step": nsym,
                    "l2": f"inputs rotate over {ring} device buffers of {x_np.nbytes >> 20} MiB "
-                         f"({ring * x_np.nbytes >> 20} MiB > 2x the 129 MB L2), no flush",
+                         f"({ring * x_np.nbytes >> 20} MiB" + (" > 2x the 129 MB L2), no flush"
+                                                               if ring * x_np.nbytes > 2 * L2_BYTES else
+                                                               ", within L2: reduced size for profiling only)"),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "aeq_mu_shift": MU_SHIFT, "rde_a": 64},
         "roofline": roof,
@@ -895,6 +897,8 @@ def main(argv=None):
     ap.add_argument("--aeq-warmup", type=int, default=None, help="cfg2 / cfg5: AEQ segment warm-up in symbols")
     ap.add_argument("--no-other-semantics", action="store_true",
                     help="cfg2: skip the extra keys timed on segmented AEQ semantics")
+    ap.add_argument("--n-sym", type=int, default=0,
+                    help="cfg2 / cfg5: symbols per polarisation (0 = the workload's; smaller only for profiling)")
     ap.add_argument("--ref-samples", type=int, default=1 << 17,
                     help="--impl reference, serial AEQ: stream prefix (samples) the oracle runs per step")
     args = ap.parse_args(argv)
@@ -902,6 +906,9 @@ def main(argv=None):
         wl["period"] = args.aeq_period
         wl["freq_sum"] = args.aeq_freq_sum
     if args.workload in WORKLOADS:
+        if args.n_sym > 0:
+            WORKLOADS[args.workload]["n_sym"] = args.n_sym
+            WORKLOADS[args.workload]["desc"] += f" [reduced to {args.n_sym} symbols per polarisation]"
         if args.aeq_segment is not None:
             WORKLOADS[args.workload]["segment"] = args.aeq_segment
         if args.aeq_warmup is not None:

@@ -361,10 +361,16 @@ FNT_API fnt_status fnt_plan_set_tensor_gradient(fnt_plan *plan, int32_t on);
  * host taps).  The work tables and the intermediate CDC -> AEQ symbols live in
  * a fixed array of about 4.3 MiB in device memory that belongs to the library
  * image: every GPU that loads libfnt holds it until the process exits.  The
- * first call on a device, with that device current, looks up the array's
- * address; make that first call before any stream capture.  All calls on a
- * device share the array and overwrite it, so calls whose work overlaps on the
- * GPU race: keep them on one stream or wait between them.  Frames longer than
+ * first call on a device, with that device current, sets up: it looks up the
+ * array's address, creates the events that guard the library's host copies of
+ * the work tables, and (once per process) page-locks those host copies; make
+ * that first call outside any stream capture.  Each call uploads its tables
+ * with one asynchronous copy and does not wait for the stream (a host copy is
+ * reused four calls later, after its last upload has run).  The call cannot be
+ * captured in a CUDA graph: on a capturing stream it returns FNT_ERR_INVALID
+ * and enqueues nothing.  All calls on a device share the array and overwrite
+ * it, so calls whose work overlaps on the GPU race: keep them on one stream or
+ * wait between them.  Frames longer than
  * FNT_NOALLOC_MAX_SAMPLES, or plans that cut one into more than
  * FNT_NOALLOC_MAX_SEGMENTS AEQ segments, are rejected with FNT_ERR_BOUND before
  * anything is enqueued.  Results equal fnt_cdc_aeq_run's bit for bit.

@@ -12,12 +12,17 @@
 // exits, and no call allocates.
 //
 // Set-up: the first call on a device, with that device current, looks up the
-// array's device address (cudaGetSymbolAddress) and keeps it for later calls on
-// that device; make that first call before any stream capture.  All calls on a
-// device share the array, so calls whose work overlaps on the GPU race on it:
-// issue them on one stream, or wait for one to finish before the next starts.
-// Nothing in the array needs to start at zero: each call rewrites the tables and
-// the CDC stage writes every intermediate symbol the AEQ stage reads.
+// array's device address (cudaGetSymbolAddress), creates the events that guard
+// the host copies of the work tables, and (once per process) page-locks those
+// host copies (cudaHostRegister); later calls on that device reuse all of it.
+// Make that first call outside any stream capture.  The call cannot itself be
+// captured in a CUDA graph: it refuses a capturing stream with FNT_ERR_INVALID,
+// because a captured table upload would read host memory that later calls
+// reuse.  All calls on a device share the array, so calls whose work overlaps
+// on the GPU race on it: issue them on one stream, or wait for one to finish
+// before the next starts.  Nothing in the array needs to start at zero: each
+// call rewrites the tables and the CDC stage writes every intermediate symbol
+// the AEQ stage reads.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,11 +61,24 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[fnt::kScratchBy
 namespace fnt {
 namespace {
 
-std::mutex g_mu;                               // guards the host staging and the address cache
+std::mutex g_mu;                               // guards the host tables, the events and the address cache
 char *g_dev_addr[kMaxDevices] = {nullptr};     // device address of the array, per device
-DevFrame g_frame;                              // host staging of the tables (no heap use)
-int4 g_items[kMaxItems];
-AeqChain g_chains[kMaxChains];
+
+// Host copies of the work tables, laid out as the array's first kOffInit bytes
+// are for a call (frame at 0, CDC items at 256, AEQ chains after them), in a
+// ring so that a call does not wait for the previous call's upload.  They are
+// page-locked once, so each call uploads its tables with one asynchronous copy
+// that never waits for the stream; before a host copy is rewritten, the event
+// recorded after its last upload is waited for (four calls earlier).
+constexpr int kMirrors = 4;
+struct alignas(4096) Mirror {   // whole pages, for cudaHostRegister
+    unsigned char bytes[kOffInit];
+};
+Mirror g_mirror[kMirrors];
+bool g_mirror_locked = false;
+cudaEvent_t g_mirror_done[kMirrors][kMaxDevices] = {};
+int g_mirror_dev[kMirrors] = {-1, -1, -1, -1};   // device of the mirror's last upload
+unsigned g_next = 0;
 
 }  // namespace
 }  // namespace fnt
@@ -96,22 +114,44 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
         return fail(FNT_ERR_BOUND, "noalloc: %lld AEQ segments exceed the fixed scratch (at most %d)",
                     (long long)n_chains, kMaxChains);
 
+    // a captured upload would read a host table that later calls rewrite
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "noalloc: cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(FNT_ERR_INVALID, "noalloc: the stream is capturing; this call cannot be captured in a graph");
+
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "noalloc: cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(FNT_ERR_INVALID, "noalloc: device %d not supported", dev);
 
     std::lock_guard<std::mutex> g(g_mu);
     if (!g_dev_addr[dev]) {
+        // set-up, once per device (and the page-locking once per process)
         void *addr = nullptr;
         e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "noalloc: cudaGetSymbolAddress");
+        for (int m = 0; m < kMirrors && e == cudaSuccess; ++m)
+            if (!g_mirror_done[m][dev]) e = cudaEventCreateWithFlags(&g_mirror_done[m][dev], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "noalloc: cudaEventCreate");
+        if (!g_mirror_locked) {
+            e = cudaHostRegister(g_mirror, sizeof g_mirror, cudaHostRegisterPortable);
+            if (e != cudaSuccess) return cuda_fail(e, "noalloc: cudaHostRegister");
+            g_mirror_locked = true;
+        }
         g_dev_addr[dev] = (char *)addr;
     }
     char *base = g_dev_addr[dev];
     if (f->n == 0) return FNT_OK;
 
-    DevFrame &df = g_frame;
+    const int mi = (int)(g_next++ % kMirrors);
+    if (g_mirror_dev[mi] >= 0) {
+        e = cudaEventSynchronize(g_mirror_done[mi][g_mirror_dev[mi]]);   // its last upload has run
+        if (e != cudaSuccess) return cuda_fail(e, "noalloc: table buffer wait");
+    }
+    unsigned char *mir = g_mirror[mi].bytes;
+    DevFrame &df = *(DevFrame *)(mir + kOffFrame);
     memset(&df, 0, sizeof df);
     df.in = (const int8_t *)f->in;
     df.out = f->out;
@@ -127,15 +167,19 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
     df.phase = phase;
     memcpy(df.taps, f->cd_taps, 2 * (size_t)f->cd_len);
 
+    int4 *items = (int4 *)(mir + kOffItems);
     const int64_t nblk = (f->n + S - 1) / S;
     int n_items = 0;
     for (int64_t b = 0; b < nblk; b += kBlocksPerItem)
         for (int pol = 0; pol < 2; ++pol)
-            g_items[n_items++] = make_int4(0, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), pol);
+            items[n_items++] = make_int4(0, (int)b, (int)std::min<int64_t>(kBlocksPerItem, nblk - b), pol);
 
+    // the chains follow the items (kOffChains bounds them for the largest frame)
+    const size_t off_chains = (kOffItems + (size_t)n_items * sizeof(int4) + 255) / 256 * 256;
+    AeqChain *chains = (AeqChain *)(mir + off_chains);
     int nc = 0;
     if (n_chains == 1) {
-        AeqChain &c = g_chains[nc++];
+        AeqChain &c = chains[nc++];
         c = AeqChain{};
         c.write_state = f->aeq_state != nullptr;
         c.end = nsym;
@@ -143,7 +187,7 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
         c.init_copy = -1;
     } else {
         for (int64_t k = 0; k < nsym; k += seg) {
-            AeqChain &c = g_chains[nc++];
+            AeqChain &c = chains[nc++];
             c = AeqChain{};
             c.keep = k;
             c.end = std::min(nsym, k + seg);
@@ -157,12 +201,10 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
         // segments are all equal but the last, so they need no longest-first sort
     }
 
-    e = cudaMemcpyAsync(base + kOffFrame, &df, sizeof df, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + kOffItems, g_items, (size_t)n_items * sizeof(int4), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess && nc > 0)
-        e = cudaMemcpyAsync(base + kOffChains, g_chains, (size_t)nc * sizeof(AeqChain), cudaMemcpyHostToDevice, stream);
+    e = cudaMemcpyAsync(base, mir, off_chains + (size_t)nc * sizeof(AeqChain), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(g_mirror_done[mi][dev], stream);
     if (e != cudaSuccess) return cuda_fail(e, "noalloc: table upload");
+    g_mirror_dev[mi] = dev;
 
     const DevFrame *frames = (const DevFrame *)(base + kOffFrame);
     const int nw = p->cdc_warps;
@@ -176,7 +218,7 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
             e = cudaMemcpyAsync(base + kOffInit, f->aeq_state, kStateBytes, cudaMemcpyDeviceToDevice, stream);
             if (e != cudaSuccess) return cuda_fail(e, "noalloc: copy initial taps");
         }
-        e = aeq_launch_for(p, frames, (const AeqChain *)(base + kOffChains), nc, stream);
+        e = aeq_launch_for(p, frames, (const AeqChain *)(base + off_chains), nc, stream);
         if (e != cudaSuccess) return cuda_fail(e, "noalloc: aeq kernel launch");
     }
     return FNT_OK;
