@@ -51,10 +51,10 @@ struct AeqCfg {
     // and spectrum memory so that more warps fit on an SM
     static constexpr int PRE = NA == 64 ? 4 : 8;
     // code-size choices: at N = 32 the fully unrolled forms are small and
-    // faster; at N = 64 one N/2-point code copy run twice and a partly unrolled
-    // gradient keep the kernel inside the instruction cache
+    // faster; at N = 64 one N/2-point code copy run twice and a gradient loop
+    // over 8-symbol runs keep the kernel inside the instruction cache
     static constexpr bool FULL_INPUT = NA == 32;             // input spectra as one N-point transform
-    static constexpr int GRAD_UNROLL = NA == 32 ? NA - kAeqK : 4;
+    static constexpr int GRAD_OUTER = NA == 32 ? (NA - kAeqK) / 8 : 1;   // 8-symbol runs unrolled
     static constexpr int XS = PRE * SA + K;                  // staged input symbols (char4 words)
     static constexpr int HALF = M + 1;                       // padded half row
     static constexpr int XF_ROW = 2 * HALF + 1;              // conflict-free: rows 3 banks apart
@@ -65,7 +65,7 @@ struct AeqCfg {
     static constexpr int KT = SA / 16;                       // k-steps of the gradient product
     static constexpr int EZ_ROW = SA / 2 + 4;                // f16 pairs per limb row; conflict-free
     static constexpr int EZH = 8 * EZ_ROW;                   // e z limbs [o, limb][SA] as f16
-    static constexpr int EZ = EZH > 3 * SA ? EZH : 3 * SA;   // ... or z [2][SA] and e [SA] as int32
+    static constexpr int EZ = EZH > 4 * SA ? EZH : 4 * SA;   // ... or e z limb pairs [2][SA] as int2
     static constexpr int WORDS = 2 * XS + XF + RED + EZ;     // xs double-buffered
     // then, at P = 1, the master taps [filter (o, s1)][k] (rows padded so that
     // 16-byte accesses are conflict-free); at P > 1 the tap half-spectra
@@ -290,8 +290,7 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
     int32_t *xf = (int32_t *)(xs2 + 2 * C::XS);
     int32_t *red = xf + C::XF;
     uint32_t *ezh = (uint32_t *)(red + C::RED);
-    int32_t *zs = (int32_t *)ezh;                 // integer gradient: z of both outputs, then e
-    int32_t *es = zs + 2 * SA;
+    int2 *ezl = (int2 *)ezh;                      // integer gradient: e z_o as limbs (c0, c1) [o][SA]
     int32_t *tsm = (int32_t *)(ezh + C::EZ);             // P = 1: the warp's master taps, [filter][TROW]
     int32_t *wcache = tsm + lane;                         // P > 1: stride 32, conflict-free
 
@@ -486,9 +485,10 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                         ez_limbs<2 * C::EZ_ROW>(mad_wide(e, z1, kLimbBias), col + 8 * C::EZ_ROW);
                     }
                 } else {
-                    zs[i] = valid ? z0 : 0;
-                    zs[SA + i] = valid ? z1 : 0;
-                    es[i] = e;
+                    // e z_o (|e z| <= 2^46) = c1 2^23 + c0, 0 <= c0 < 2^23, |c1| <= 2^23
+                    const int64_t ez0 = (int64_t)e * z0, ez1 = (int64_t)e * z1;
+                    ezl[i] = make_int2((int32_t)(ez0 & 0x7FFFFF), (int32_t)(ez0 >> 23));
+                    ezl[SA + i] = make_int2((int32_t)(ez1 & 0x7FFFFF), (int32_t)(ez1 >> 23));
                 }
             }
             __syncwarp();
@@ -513,23 +513,35 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                     __syncwarp();                         // gs is rewritten by the next block
                 } else {
                     // taps k0 .. k0 + 3 over a rolling window w0..w3 = x_S1[t0 + i - k0 - kk],
-                    // read as sign-extending byte loads of stream s1 from the staged words
+                    // read as sign-extending byte loads of stream s1 from the staged words;
+                    // G = sum_i (c1_i 2^23 + c0_i) w: the limb sums run in int32 over 8
+                    // symbols at a time (below 8 2^23 16 = 2^30, exact) and then fold
+                    // into the int64 sums
                     const int8_t *xb = (const int8_t *)(xs + bb * SA + K - k0) + s1;
                     int32_t w1 = xb[-4], w2 = xb[-8], w3 = xb[-12];
-                    const int32_t *zrow = zs + o * SA;
-#pragma unroll C::GRAD_UNROLL
-                    for (int i = 0; i < SA; ++i) {
-                        const int32_t w0 = xb[4 * i];
-                        const int32_t e = es[i];
-                        const int32_t z = zrow[i];
-                        // |z w| <= 2^19: 32-bit product; e (z w) + acc in one wide multiply-add
-                        acc[0] = mad_wide(e, z * w0, acc[0]);
-                        acc[1] = mad_wide(e, z * w1, acc[1]);
-                        acc[2] = mad_wide(e, z * w2, acc[2]);
-                        acc[3] = mad_wide(e, z * w3, acc[3]);
-                        w3 = w2;
-                        w2 = w1;
-                        w1 = w0;
+                    const int2 *ezrow = ezl + o * SA;
+#pragma unroll C::GRAD_OUTER
+                    for (int i8 = 0; i8 < SA; i8 += 8) {
+                        int32_t l0[4] = {0, 0, 0, 0}, l1[4] = {0, 0, 0, 0};
+#pragma unroll
+                        for (int ii = 0; ii < 8; ++ii) {
+                            const int i = i8 + ii;
+                            const int32_t w0 = xb[4 * i];
+                            const int2 c = ezrow[i];
+                            l0[0] += c.x * w0;
+                            l1[0] += c.y * w0;
+                            l0[1] += c.x * w1;
+                            l1[1] += c.y * w1;
+                            l0[2] += c.x * w2;
+                            l1[2] += c.y * w2;
+                            l0[3] += c.x * w3;
+                            l1[3] += c.y * w3;
+                            w3 = w2;
+                            w2 = w1;
+                            w1 = w0;
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) acc[kk] += ((int64_t)l1[kk] << 23) + l0[kk];
                     }
                 }
                 if (apply) {
