@@ -151,13 +151,20 @@ FNT_API fnt_status fnt_plan_destroy(fnt_plan *plan);
  *                         polarisation, for a frame with cd_len taps
  *                         (2 N per block, S / 2 symbols per block at 2 sps)
  *   aeq_mults_per_symbol  pointwise products of the 4x4 AEQ per symbol
- *                         (32 N_aeq per block of N_aeq - 16 symbols)
- * At the operating point of Tab. 1 (CDC N = 64 with 50 % overlap, i.e.
- * cdc_step = 32; AEQ N = 32) these are 8 and 64. */
+ *                         (32 N_aeq per block of N_aeq - 16 symbols) on the
+ *                         warp-per-chain kernel
+ *   aeq_cta_mults_per_symbol  the same on the CTA-per-chain kernel
+ * The products are counted from the kernels' own product stages: the library
+ * runs the templates those kernels execute, on the host, with an arithmetic
+ * policy that counts instead of computing; power-of-two multiplications
+ * (eq. (8)'s -2^8) count as shifts.  At the operating point of Tab. 1 (CDC
+ * N = 64 with 50 % overlap, i.e. cdc_step = 32; AEQ N = 32) these are 8, 64
+ * and 64. */
 typedef struct fnt_op_counts {
     double cdc_mults_per_symbol;
     double aeq_mults_per_symbol;
     double cdc_butterflies_per_symbol;
+    double aeq_cta_mults_per_symbol;
 } fnt_op_counts;
 
 FNT_API fnt_status fnt_op_counts_for(const fnt_plan_desc *desc, int32_t cd_len, fnt_op_counts *out);

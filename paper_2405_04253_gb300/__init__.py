@@ -49,7 +49,7 @@ class BatchC(ctypes.Structure):
 
 class OpCounts(ctypes.Structure):
     _fields_ = [("cdc_mults_per_symbol", ctypes.c_double), ("aeq_mults_per_symbol", ctypes.c_double),
-                ("cdc_butterflies_per_symbol", ctypes.c_double)]
+                ("cdc_butterflies_per_symbol", ctypes.c_double), ("aeq_cta_mults_per_symbol", ctypes.c_double)]
 
 
 class Completion(ctypes.Structure):

@@ -430,8 +430,7 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                 for (int j = 0; j < M; ++j) y[j] = wcache[32 * j];
             }
             const int32_t *xrow = xf + (bb * 4 + s1) * C::XF_ROW + h * C::HALF;
-#pragma unroll
-            for (int j = 0; j < M; ++j) y[j] = rho(rhoc(y[j]) * xrow[j]);
+            spectral_products(ZArith{}, y, xrow);
             if (FS && fsum) {
                 // frequency-domain summation: the four input lanes of an (output,
                 // group, half) all hold the sum of their products in Z_F
@@ -598,9 +597,22 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
 
 }  // namespace
 
-// Pointwise products mod F per AEQ block of both polarisations: 16 filters x 2
-// tap groups x N (each split over two lanes as two N/2 halves).
-int aeq_mults_per_block(int na) { return 32 * na; }
+// Pointwise products mod F per AEQ block of both polarisations: every lane of
+// a polarisation's warp runs the product stage of its task's N/2-point half
+// once per block (16 tasks x 2 halves = 32 lanes); the stage is the kernel's
+// own spectral_products, executed on the host with the counting policy.
+template <int NA>
+static int aeq_lane_products() {
+    int mults = 0, shifts = 0;
+    int32_t y[NA / 2] = {}, x[NA / 2] = {};
+    spectral_products(CountArith{&mults, &shifts}, y, x);
+    return mults;
+}
+
+int aeq_mults_per_block(int na) {
+    constexpr int kLanesPerPol = 32;
+    return 2 * kLanesPerPol * (na == 64 ? aeq_lane_products<64>() : aeq_lane_products<32>());
+}
 
 size_t aeq_smem_bytes(int na, int warps, int period) {
     const int words = na == 64 ? AeqCfg<64, 4080>::WORDS + (period > 1 ? AeqCfg<64, 4080>::WCACHE : AeqCfg<64, 4080>::TAPS)

@@ -111,6 +111,26 @@ __device__ __forceinline__ int32_t mulred(int32_t a, int32_t b) {
     return (int32_t)(t >> 32) + (int32_t)(lo & 0xFFFFu) - (int32_t)(lo >> 16);
 }
 
+// The Z_F arithmetic of this kernel's product stage (64-bit product reduced
+// by mulred), as a policy so that the host can count the products.
+struct RedArith {
+    __device__ __forceinline__ int32_t mulmod(int32_t a, int32_t h) const { return mulred(a, h); }
+};
+
+// One thread's piece of a pointwise product: u[i] <- u[i] X_in[i], the input
+// spectrum row read 16 bytes at a time.
+template <class A, int NP>
+FNT_HD void piece_products(const A &ar, int32_t (&u)[NP], const int32_t *xrow) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 4) {
+        const int4 x4 = *(const int4 *)(xrow + i);
+        u[i] = ar.mulmod(u[i], x4.x);
+        u[i + 1] = ar.mulmod(u[i + 1], x4.y);
+        u[i + 2] = ar.mulmod(u[i + 2], x4.z);
+        u[i + 3] = ar.mulmod(u[i + 3], x4.w);
+    }
+}
+
 // Byte J of w (J runtime), sign-extended.
 __device__ __forceinline__ int32_t sbyte_rt(uint32_t w, uint32_t sel) {
     int32_t r;
@@ -313,14 +333,7 @@ __global__ void __launch_bounds__(SerCfg<NA, ALPHA>::NTHR, 1)
                         }
                         fnt_fwd<NP, C::BETA, 17>(u);
                         const int32_t *xrow = xf + bb * C::XBLK + ps1 * C::S1STR + r * C::XROW;
-#pragma unroll
-                        for (int i = 0; i < NP; i += 4) {
-                            const int4 x4 = *(const int4 *)(xrow + i);
-                            u[i] = mulred(u[i], x4.x);
-                            u[i + 1] = mulred(u[i + 1], x4.y);
-                            u[i + 2] = mulred(u[i + 2], x4.z);
-                            u[i + 3] = mulred(u[i + 3], x4.w);
-                        }
+                        piece_products(RedArith{}, u, xrow);
                         fnt_inv<NP, C::BETA, 17>(u);
                         int32_t *trows = tb + task * C::TT;
                         trows[r] = rho(u[0]);
@@ -442,6 +455,22 @@ size_t serial_smem() {
 }
 
 }  // namespace
+
+// Pointwise products per AEQ block of both polarisations on this kernel: the
+// 16 R threads of a polarisation's phase 1 each run the product stage of their
+// N/R-point piece once per block (the stage counted on the host).
+template <int NA, int64_t ALPHA>
+static int serial_mults_per_block() {
+    using C = SerCfg<NA, ALPHA>;
+    int mults = 0, shifts = 0;
+    int32_t u[C::NP] = {}, x[C::NP] = {};
+    piece_products(CountArith{&mults, &shifts}, u, x);
+    return 2 * 16 * C::R * mults;
+}
+
+int aeq_serial_mults_per_block(int na) {
+    return na == 64 ? serial_mults_per_block<64, 4080>() : serial_mults_per_block<32, 2>();
+}
 
 size_t aeq_serial_smem_bytes(int na) { return na == 64 ? serial_smem<64, 4080>() : serial_smem<32, 2>(); }
 

@@ -237,6 +237,7 @@ extern "C" fnt_status fnt_op_counts_for(const fnt_plan_desc *d, int32_t cd_len, 
     out->cdc_mults_per_symbol = cdc_mults_per_block() / sym_per_block;
     out->cdc_butterflies_per_symbol = cdc_butterflies_per_block() / sym_per_block;
     out->aeq_mults_per_symbol = (double)aeq_mults_per_block(d->n_aeq) / (d->n_aeq - kAeqK);
+    out->aeq_cta_mults_per_symbol = (double)aeq_serial_mults_per_block(d->n_aeq) / (d->n_aeq - kAeqK);
     return FNT_OK;
 }
 

@@ -46,6 +46,32 @@ __device__ __forceinline__ void cp_async4(uint32_t *smem, const uint32_t *gmem, 
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Eqs. (7)/(8) on the two product spectra: P <- P + Q (z_re's spectrum, 2^-1
+// N^-1 folded into H) and Q <- -2^8 (P - Q) (z_im's: 2^-9 = 2^-1 (-2^8)).
+template <class A>
+FNT_HD void cdc_combine(const A &ar, int32_t (&P)[kN], int32_t (&Q)[kN]) {
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+        const int32_t a = P[i] + Q[i];
+        const int32_t b = P[i] - Q[i];
+        P[i] = rho(a);
+        Q[i] = ar.mulpow2(b, -256);
+    }
+}
+
+// The spectral stage of a block: the pointwise products with the tap spectra
+// (H_u, H_v at hs, hs + N) and eqs. (7)/(8).  make_q forms v and its transform
+// in Q between the two products, which keeps P's product ahead of Q's
+// transform (fewer live registers).  The kernel runs the stage with ZArith;
+// the host runs the same code with a counting policy for the Tab. 1 counts.
+template <class A, class MakeQ>
+FNT_HD void cdc_spectral_stage(const A &ar, int32_t (&P)[kN], int32_t (&Q)[kN], const int32_t *hs, MakeQ make_q) {
+    spectral_products(ar, P, hs);
+    make_q(Q);
+    spectral_products(ar, Q, hs + kN);
+    cdc_combine(ar, P, Q);
+}
+
 // One block of one polarisation: window words w[j] = win[j][lane]; results
 // (re, im) as int16 into o[j][lane] for all 64 window positions.  `o` may be
 // `win` itself: every output depends on every input of the lane's column, so
@@ -59,23 +85,14 @@ __device__ __forceinline__ void cdc_block(const uint32_t *win, uint32_t *o, cons
         P[j] = sx8(w, sh) + 256 * sx8(w, sh + 8);
     }
     fnt_fwd<kN, kAlpha, 13>(P);                      // |u| <= 16 + 256 * 16 < 2^13
+    cdc_spectral_stage(ZArith{}, P, Q, hs, [&](int32_t (&q)[kN]) {
 #pragma unroll
-    for (int i = 0; i < kN; ++i) P[i] = rho(rhoc(P[i]) * hs[i]);
-#pragma unroll
-    for (int j = 0; j < kN; ++j) {
-        const uint32_t w = win[j * kRow + lane];
-        Q[j] = sx8(w, sh) - 256 * sx8(w, sh + 8);
-    }
-    fnt_fwd<kN, kAlpha, 13>(Q);
-#pragma unroll
-    for (int i = 0; i < kN; ++i) Q[i] = rho(rhoc(Q[i]) * hs[kN + i]);
-#pragma unroll
-    for (int i = 0; i < kN; ++i) {
-        const int32_t a = P[i] + Q[i];
-        const int32_t b = P[i] - Q[i];
-        P[i] = rho(a);              // eq. (7) spectrum (2^-1 N^-1 folded into H)
-        Q[i] = rho(b * -256);       // eq. (8) spectrum: 2^-9 = 2^-1 * (-2^8)
-    }
+        for (int j = 0; j < kN; ++j) {
+            const uint32_t w = win[j * kRow + lane];
+            q[j] = sx8(w, sh) - 256 * sx8(w, sh + 8);
+        }
+        fnt_fwd<kN, kAlpha, 13>(q);
+    });
     int16_t *o16 = (int16_t *)o;
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
@@ -239,9 +256,15 @@ __global__ void __launch_bounds__(128, BOTH ? 2 : 3) cdc_kernel(const DevFrame *
 
 size_t cdc_smem_bytes(int warps) { return (size_t)warps * kWarpWords * sizeof(uint32_t); }
 
-// Pointwise products mod F that cdc_block performs per overlap-save block and
-// polarisation (P = FNT(u) H_u and Q = FNT(v) H_v), and its transform butterflies.
-int cdc_mults_per_block() { return 2 * kN; }
+// Pointwise products mod F per overlap-save block and polarisation (P = FNT(u)
+// H_u and Q = FNT(v) H_v): the spectral stage the kernel runs (cdc_block),
+// executed on the host with the counting policy.
+int cdc_mults_per_block() {
+    int mults = 0, shifts = 0;
+    int32_t P[kN] = {}, Q[kN] = {}, hs[2 * kN] = {};
+    cdc_spectral_stage(CountArith{&mults, &shifts}, P, Q, hs, [](int32_t (&)[kN]) {});
+    return mults;
+}
 int cdc_butterflies_per_block() { return 4 * (kN / 2) * 6; }
 
 cudaError_t cdc_configure() {

@@ -103,6 +103,7 @@ cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, i
 size_t aeq_min_smem(const fnt_plan *p);   // shared memory per AEQ CTA that enforces the occupancy cap
 // The CTA-per-chain AEQ kernel (aeq_serial.cu): few long chains, latency per block.
 size_t aeq_serial_smem_bytes(int na);
+int aeq_serial_mults_per_block(int na);
 cudaError_t aeq_serial_configure();
 cudaError_t aeq_serial_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,
                               int grid, cudaStream_t stream);

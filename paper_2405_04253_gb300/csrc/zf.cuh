@@ -99,6 +99,34 @@ FNT_HD int32_t decode(int32_t x) {
 // Runtime variant for a centred constant w (|w| <= 2^15) and |x| < 2^30.
 FNT_HD int32_t mulw(int32_t x, int32_t w) { return rho(rhoc(x) * w); }
 
+// ------------------------------------------------------ spectral products ----
+//
+// The pointwise spectrum products of the kernels go through an arithmetic
+// policy: ZArith is what the kernels run, and the host instantiates the same
+// templates with a counting policy to report how many multiplications the
+// kernels' product stages issue (the counts of Tab. 1).  mulmod is a product of
+// two arbitrary residues; mulpow2 multiplies by a signed power of two (a shift
+// in the paper's cost model, which Tab. 1 does not count).
+struct ZArith {
+    FNT_HD int32_t mulmod(int32_t a, int32_t h) const { return rho(rhoc(a) * h); }   // |a| < 2^30, |h| <= 2^15
+    FNT_HD int32_t mulpow2(int32_t a, int32_t c) const { return rho(a * c); }         // |a c| < 2^31
+};
+
+// Host policy that counts, instead of computing: general products in *mults,
+// power-of-two multiplications in *shifts.
+struct CountArith {
+    int *mults, *shifts;
+    FNT_HD int32_t mulmod(int32_t, int32_t) const { return ++*mults, 0; }      // host use only
+    FNT_HD int32_t mulpow2(int32_t, int32_t) const { return ++*shifts, 0; }
+};
+
+// x[i] <- x[i] h[i] (mod F), i < N: one transform's pointwise product.
+template <class A, int N>
+FNT_HD void spectral_products(const A &ar, int32_t (&x)[N], const int32_t *h) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = ar.mulmod(x[i], h[i]);
+}
+
 // -------------------------------------------------------------- transforms ----
 //
 // Lazy reduction.  Every register of a transform carries a compile-time bound

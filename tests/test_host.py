@@ -202,15 +202,20 @@ def test_single_rank_reduce_is_identity():
 
 def test_tab1_multiplication_counts():
     """Tab. 1: FNT-CDC 8 and FNT-AEQ 64 real multiplications per symbol at the
-    paper's operating point (64-point CDC with 50 % overlap, 32-point AEQ),
-    from the kernels' own per-block counts.  The FD / TD rows and the
-    complexity reductions of the text are context (evaluated here from the
-    table's formulas)."""
+    paper's operating point (64-point CDC with 50 % overlap, 32-point AEQ).
+    The library counts them by running the product-stage templates the
+    kernels execute (the CDC's spectral stage, each AEQ kernel's product
+    stage) on the host with a counting arithmetic policy, so a product added
+    to a kernel's product stage changes these numbers.  The FD / TD rows and
+    the complexity reductions of the text are context (evaluated here from
+    the table's formulas)."""
     import math
     import paper_2405_04253_gb300 as fnt
     oc = fnt.op_counts(17, cdc_step=32, n_aeq=32, alpha_aeq=2)
     assert oc["cdc_mults_per_symbol"] == 8
     assert oc["aeq_mults_per_symbol"] == 64
+    assert oc["aeq_cta_mults_per_symbol"] == 64
+    assert fnt.op_counts(17, n_aeq=64, alpha_aeq=4080)["aeq_cta_mults_per_symbol"] == 32 * 64 / 48
     fd_cdc = lambda n: 12 * math.log2(n) + 12
     fd_aeq = lambda n: 24 * math.log2(n) + 32
     assert round(1 - 64 / fd_aeq(32), 2) == 0.58                    # AEQ: -58 %
