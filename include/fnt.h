@@ -320,14 +320,17 @@ FNT_API fnt_status fnt_plan_set_aeq_occupancy(fnt_plan *plan, int32_t max_warps_
  * polarisation), which spreads each block of the serial recurrence of eq. (6)
  * (section "Proposed FNT-CDC&AEQ structure") over 288 threads and cuts the time
  * per block of a lone chain; 0 (default) = 2 when the launch's chains fit one
- * CTA per SM, else 1.  Plans with aeq_freq_sum != 0 always use 1.  Results do
- * not depend on it.  FNT_ERR_INVALID outside [0, 2]. */
+ * CTA per SM and its longest chain has at least 256 AEQ blocks, else 1 (short
+ * chains, such as the segments of served frames, do better in 1 when several
+ * launches share the GPU, as each CTA of 2 holds a whole SM).  Plans with
+ * aeq_freq_sum != 0 always use 1.  Results do not depend on it.
+ * FNT_ERR_INVALID outside [0, 2]. */
 FNT_API fnt_status fnt_plan_set_aeq_kernel(fnt_plan *plan, int32_t kind);
 
 /* The AEQ kernel (1 or 2, as above) a launch of `n_chains` AEQ chains of this
- * plan takes; 0 for a null plan.  A chain is a frame, or one AEQ segment of a
- * frame. */
-FNT_API int32_t fnt_plan_aeq_kernel_for(const fnt_plan *plan, int64_t n_chains);
+ * plan, the longest of `longest_symbols` symbols, takes; 0 for a null plan.
+ * A chain is a frame, or one AEQ segment of a frame with its warm-up. */
+FNT_API int32_t fnt_plan_aeq_kernel_for(const fnt_plan *plan, int64_t n_chains, int64_t longest_symbols);
 
 /* The plan's initial AEQ taps (the state a frame without aeq_state, or a newly
  * configured serving link, starts from): HOST int32 [4 (S2)][4 (S1)][16],

@@ -89,7 +89,7 @@ SIGNATURES = {
     "fnt_plan_initial_taps": (_I32, [_VP, _VP]),
     "fnt_plan_set_aeq_occupancy": (_I32, [_VP, _I32]),
     "fnt_plan_set_aeq_kernel": (_I32, [_VP, _I32]),
-    "fnt_plan_aeq_kernel_for": (_I32, [_VP, _I64]),
+    "fnt_plan_aeq_kernel_for": (_I32, [_VP, _I64, _I64]),
     "fnt_op_counts_for": (_I32, [ctypes.POINTER(PlanDesc), _I32, ctypes.POINTER(OpCounts)]),
     "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
     "fnt_aeq_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
@@ -211,9 +211,10 @@ class Plan:
         0 automatic; same results."""
         check(lib().fnt_plan_set_aeq_kernel(self.handle, int(kind)))
 
-    def aeq_kernel_for(self, n_chains: int) -> int:
-        """The AEQ kernel (1 or 2) a launch of n_chains chains takes."""
-        return int(lib().fnt_plan_aeq_kernel_for(self.handle, int(n_chains)))
+    def aeq_kernel_for(self, n_chains: int, longest_symbols: int) -> int:
+        """The AEQ kernel (1 or 2) a launch of n_chains chains, the longest of
+        longest_symbols symbols, takes."""
+        return int(lib().fnt_plan_aeq_kernel_for(self.handle, int(n_chains), int(longest_symbols)))
 
     def initial_state(self) -> np.ndarray:
         """The plan's initial AEQ taps, int32 [4 (S2)][4 (S1)][16]."""

@@ -270,23 +270,29 @@ extern "C" fnt_status fnt_plan_set_aeq_kernel(fnt_plan *p, int32_t kind) {
     return FNT_OK;
 }
 
-extern "C" int32_t fnt_plan_aeq_kernel_for(const fnt_plan *p, int64_t n_chains) {
+extern "C" int32_t fnt_plan_aeq_kernel_for(const fnt_plan *p, int64_t n_chains, int64_t longest_symbols) {
     if (!p) return 0;
-    return aeq_use_serial(p, (int)std::min<int64_t>(n_chains, INT32_MAX)) ? 2 : 1;
+    return aeq_use_serial(p, n_chains, longest_symbols) ? 2 : 1;
 }
 
-// The CTA-per-chain kernel holds one (chain, polarisation) per SM: it is taken
-// when that many fit in one wave, and only for per-pair inverse transforms.
-bool fnt::aeq_use_serial(const fnt_plan *p, int n_chains) {
+// The CTA-per-chain kernel holds one (chain, polarisation) per SM.  It is taken
+// when that many fit in one wave and the longest chain is long enough for its
+// shorter block time to matter (short chains, such as the segments of a
+// served frame, finish sooner in the warp kernel once several launches share
+// the GPU, since each CTA holds a whole SM), and only for per-pair inverse
+// transforms.
+bool fnt::aeq_use_serial(const fnt_plan *p, int64_t n_chains, int64_t longest_symbols) {
     if (p->d.aeq_freq_sum != 0 || p->aeq_kernel == 1) return false;
     if (p->aeq_kernel == 2) return true;
-    return 2 * (int64_t)n_chains <= (int64_t)p->n_sm * kSerialCtasPerSm;
+    const int64_t blocks = (longest_symbols + (p->d.n_aeq - kAeqK) - 1) / (p->d.n_aeq - kAeqK);
+    return 2 * n_chains <= (int64_t)p->n_sm * kSerialCtasPerSm && blocks >= kSerialMinBlocks;
 }
 
 cudaError_t fnt::aeq_launch_for(const fnt_plan *p, const DevFrame *frames, const AeqChain *chains, int n_chains,
-                                cudaStream_t stream) {
+                                int64_t longest_symbols, cudaStream_t stream) {
     AeqParams prm{p->d.mu_shift, p->d.rde_a, update_period(p->d), p->tensor_gradient, p->d.aeq_freq_sum};
-    if (aeq_use_serial(p, n_chains)) return aeq_serial_launch(p->d.n_aeq, frames, chains, n_chains, prm, 0, stream);
+    if (aeq_use_serial(p, n_chains, longest_symbols))
+        return aeq_serial_launch(p->d.n_aeq, frames, chains, n_chains, prm, 0, stream);
     return aeq_launch(p->d.n_aeq, frames, chains, n_chains, prm, p->aeq_warps, 0, stream, aeq_min_smem(p));
 }
 
@@ -645,7 +651,9 @@ static fnt_status launch_aeq_range(const fnt_plan *p, const Work &w, const char 
                                    cudaStream_t stream) {
     if (c1 <= c0) return FNT_OK;
     const DevFrame *frames = (const DevFrame *)(dev + w.off_frames);
-    cudaError_t e = aeq_launch_for(p, frames, (const AeqChain *)(dev + w.off_chains) + c0, c1 - c0, stream);
+    int64_t longest = 0;                  // chains are sorted longest first within a chunk; take the max anyway
+    for (int c = c0; c < c1; ++c) longest = std::max(longest, w.chains[c].end - w.chains[c].begin);
+    cudaError_t e = aeq_launch_for(p, frames, (const AeqChain *)(dev + w.off_chains) + c0, c1 - c0, longest, stream);
     return e == cudaSuccess ? FNT_OK : cuda_fail(e, "aeq kernel launch");
 }
 

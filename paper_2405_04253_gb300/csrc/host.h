@@ -88,6 +88,7 @@ int work_kernel_count(const Work &w);
 // kernels
 constexpr int kCdcCtasPerSm = 3;     // cdc_kernel's __launch_bounds__ minimum
 constexpr int kSerialCtasPerSm = 1;  // aeq_serial_kernel CTAs resident per SM (registers)
+constexpr int kSerialMinBlocks = 256;  // shortest longest-chain (blocks) for which the automatic choice takes it
 size_t cdc_smem_bytes(int warps);
 int cdc_mults_per_block();
 int cdc_butterflies_per_block();
@@ -107,10 +108,11 @@ int aeq_serial_mults_per_block(int na);
 cudaError_t aeq_serial_configure();
 cudaError_t aeq_serial_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,
                               int grid, cudaStream_t stream);
-// Whether a launch of n_chains chains takes the CTA-per-chain kernel.
-bool aeq_use_serial(const fnt_plan *p, int n_chains);
-// Launches the AEQ kernel the plan picks for n_chains chains.
+// Whether a launch of n_chains chains, the longest of longest_symbols symbols,
+// takes the CTA-per-chain kernel.
+bool aeq_use_serial(const fnt_plan *p, int64_t n_chains, int64_t longest_symbols);
+// Launches the AEQ kernel the plan picks for those chains.
 cudaError_t aeq_launch_for(const fnt_plan *p, const DevFrame *frames, const AeqChain *chains, int n_chains,
-                           cudaStream_t stream);
+                           int64_t longest_symbols, cudaStream_t stream);
 
 }  // namespace fnt

@@ -218,7 +218,9 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
             e = cudaMemcpyAsync(base + kOffInit, f->aeq_state, kStateBytes, cudaMemcpyDeviceToDevice, stream);
             if (e != cudaSuccess) return cuda_fail(e, "noalloc: copy initial taps");
         }
-        e = aeq_launch_for(p, frames, (const AeqChain *)(base + off_chains), nc, stream);
+        int64_t longest = 0;
+        for (int c = 0; c < nc; ++c) longest = std::max(longest, chains[c].end - chains[c].begin);
+        e = aeq_launch_for(p, frames, (const AeqChain *)(base + off_chains), nc, longest, stream);
         if (e != cudaSuccess) return cuda_fail(e, "noalloc: aeq kernel launch");
     }
     return FNT_OK;

@@ -74,7 +74,7 @@ def test_cfg2_stream_serial_recurrence_whole_output(orc):
     kw = dict(n_aeq=64, alpha_aeq=4080, mu_shift=MU)
     plan = F.Plan(**kw)
     nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
-    assert plan.aeq_kernel_for(1) == 2
+    assert plan.aeq_kernel_for(1, nsym) == 2
     out = torch.full((nsym, 4), 0x4444, dtype=torch.int16, device="cuda")
     T0 = orc.aeq_init_taps(16, 2048)
     st = torch.from_numpy(T0).cuda()

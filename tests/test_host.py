@@ -286,7 +286,7 @@ def test_every_entry_point_rejects_null_handles_without_gpu():
     for name in ("fnt_plan_destroy", "fnt_batch_destroy", "fnt_session_destroy"):
         assert getattr(L, name)(None) == fnt.FNT_OK, name
     assert L.fnt_batch_kernel_count(None) == 0
-    assert L.fnt_plan_aeq_kernel_for(None, 1) == 0
+    assert L.fnt_plan_aeq_kernel_for(None, 1, 1 << 20) == 0
     assert L.fnt_session_pending(None) == 0
     assert fnt.last_error()                  # the last failure left its text
     decl = set(header_functions())
