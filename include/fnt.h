@@ -327,6 +327,16 @@ FNT_API fnt_status fnt_plan_set_aeq_occupancy(fnt_plan *plan, int32_t max_warps_
  * FNT_ERR_INVALID outside [0, 2]. */
 FNT_API fnt_status fnt_plan_set_aeq_kernel(fnt_plan *plan, int32_t kind);
 
+/* Picks the CDC kernel of later launches of this plan: 1 = one overlap-save
+ * block per lane (each 64-point transform in one thread's registers), the
+ * throughput layout; 2 = one block per 8 threads, each transform run as a
+ * four-step 8 x 8 transform over them (eqs. (1)/(2) split by index, section
+ * "Fermat number transform"), for work too small to fill the GPU one block per
+ * lane; 0 (default) = 2 when a launch has fewer 32-block work items than twice
+ * the SM count, else 1.  Results do not depend on it.  FNT_ERR_INVALID
+ * outside [0, 2]. */
+FNT_API fnt_status fnt_plan_set_cdc_kernel(fnt_plan *plan, int32_t kind);
+
 /* The AEQ kernel (1 or 2, as above) a launch of `n_chains` AEQ chains of this
  * plan, the longest of `longest_symbols` symbols, takes; 0 for a null plan.
  * A chain is a frame, or one AEQ segment of a frame with its warm-up. */

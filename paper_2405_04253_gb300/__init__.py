@@ -89,6 +89,7 @@ SIGNATURES = {
     "fnt_plan_initial_taps": (_I32, [_VP, _VP]),
     "fnt_plan_set_aeq_occupancy": (_I32, [_VP, _I32]),
     "fnt_plan_set_aeq_kernel": (_I32, [_VP, _I32]),
+    "fnt_plan_set_cdc_kernel": (_I32, [_VP, _I32]),
     "fnt_plan_aeq_kernel_for": (_I32, [_VP, _I64, _I64]),
     "fnt_op_counts_for": (_I32, [ctypes.POINTER(PlanDesc), _I32, ctypes.POINTER(OpCounts)]),
     "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
@@ -210,6 +211,11 @@ class Plan:
         """AEQ kernel: 1 a warp per (chain, polarisation), 2 a CTA per one,
         0 automatic; same results."""
         check(lib().fnt_plan_set_aeq_kernel(self.handle, int(kind)))
+
+    def set_cdc_kernel(self, kind: int):
+        """CDC kernel: 1 a block per lane, 2 a block per 8 threads, 0
+        automatic; same results."""
+        check(lib().fnt_plan_set_cdc_kernel(self.handle, int(kind)))
 
     def aeq_kernel_for(self, n_chains: int, longest_symbols: int) -> int:
         """The AEQ kernel (1 or 2) a launch of n_chains chains, the longest of

@@ -270,6 +270,20 @@ extern "C" fnt_status fnt_plan_set_aeq_kernel(fnt_plan *p, int32_t kind) {
     return FNT_OK;
 }
 
+extern "C" fnt_status fnt_plan_set_cdc_kernel(fnt_plan *p, int32_t kind) {
+    if (!p) return fail(FNT_ERR_INVALID, "null plan");
+    if (kind < 0 || kind > 2) return fail(FNT_ERR_INVALID, "CDC kernel must be 0 (auto), 1 or 2");
+    p->cdc_kernel = kind;
+    return FNT_OK;
+}
+
+// One block per lane needs many blocks to fill the GPU; with fewer work items
+// than two per SM, a block per 8 threads (8 warps per item) is taken instead.
+bool fnt::cdc_use_split(const fnt_plan *p, int64_t n_items) {
+    if (p->cdc_kernel != 0) return p->cdc_kernel == 2;
+    return n_items < 2 * (int64_t)p->n_sm;
+}
+
 extern "C" int32_t fnt_plan_aeq_kernel_for(const fnt_plan *p, int64_t n_chains, int64_t longest_symbols) {
     if (!p) return 0;
     return aeq_use_serial(p, n_chains, longest_symbols) ? 2 : 1;
@@ -634,7 +648,7 @@ static fnt_status launch_cdc_range(const fnt_plan *p, const Work &w, const char 
     const int n = i1 - i0;
     const int grid = std::min((n + nw - 1) / nw, p->n_sm * 64);
     cudaError_t e = cdc_launch(frames, (const int4 *)(dev + w.off_items) + i0, n, w.op == FNT_OP_CHAIN, w.cdc_both,
-                               nw, grid, stream);
+                               nw, grid, stream, cdc_use_split(p, (int64_t)w.items.size()));
     return e == cudaSuccess ? FNT_OK : cuda_fail(e, "cdc kernel launch");
 }
 

@@ -19,6 +19,8 @@
 // 8-byte (CDC) or 4-byte (chain) stores.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "zf.cuh"
 
@@ -252,6 +254,164 @@ __global__ void __launch_bounds__(128, BOTH ? 2 : 3) cdc_kernel(const DevFrame *
     }
 }
 
+// ------------------------------------------------------- small work ----
+//
+// When the work has too few blocks to give every SM a few warps at one block
+// per lane (a single 65,536-sample frame is 1366 blocks: 43 warps), a block is
+// split over 8 threads instead.  Each 64-point transform runs as a four-step
+// 8 x 8 transform: with j = 8 j1 + j2 and k = k1 + 8 k2,
+//   X[k1 + 8 k2] = sum_j2 beta^(j2 k2) alpha^(j2 k1) sum_j1 beta^(j1 k1) x[8 j1 + j2],
+// beta = alpha^8, so thread j2 transforms its 8 samples (stride 8), applies the
+// twiddles alpha^(j2 k1), and after a transpose through shared memory thread k1
+// transforms over j2 and holds X[k1 + 8 k2].  Products with the tap spectra and
+// eqs. (7)/(8) are local; each inverse runs the same four steps with
+// alpha^-1, leaving z[n2 + 8 n1] in thread n2.  The work items are the same
+// 32-block items: eight warps take an item, four blocks each.
+constexpr int kSplitBlocksPerWarp = 4;
+constexpr int kSplitWarpsPerItem = kBlocksPerItem / kSplitBlocksPerWarp;
+constexpr int kSplitTP = 9;                                // transpose row pitch (words)
+constexpr int kSplitWarpWords = kSplitBlocksPerWarp * 2 * 8 * kSplitTP;
+constexpr int kSplitWarps = 2;                             // warps per CTA
+constexpr int64_t kBeta = zpow(kAlpha, 8);                 // order 8
+
+__device__ __forceinline__ int br3(int i) { return ((i & 1) << 2) | (i & 2) | ((i >> 2) & 1); }
+
+// a b (mod F) as a lazy residue for |a| < 2^18, |b| <= 2^15 + 8: the 64-bit
+// product is hi 2^32 + lo with 2^32 = 1 and 2^16 = -1 (mod F).
+__device__ __forceinline__ int32_t mulred64(int32_t a, int32_t b) {
+    const int64_t t = (int64_t)a * b;
+    const uint32_t lo = (uint32_t)t;
+    return (int32_t)(t >> 32) + (int32_t)(lo & 0xFFFFu) - (int32_t)(lo >> 16);
+}
+
+__device__ __forceinline__ int32_t centred64(int64_t v) {
+    v %= kF;
+    if (v < 0) v += kF;
+    return v > 32768 ? (int32_t)(v - kF) : (int32_t)v;
+}
+
+// Steps B and C of the four-step transform: twiddle the 8 values (register i of
+// step A) by tw[i], write them to row br3(i) (ROW_BR) or row i, column t, of the
+// block's 8 x 8 buffer, then read row t in bit-reversed (READ_BR) or natural
+// column order for step D.
+template <bool ROW_BR, bool READ_BR>
+__device__ __forceinline__ void split_exchange(int32_t (&x)[8], const int32_t (&tw)[8], int32_t *T, int t) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) T[(ROW_BR ? br3(i) : i) * kSplitTP + t] = mulred64(x[i], tw[i]);   // < 2^17
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = T[t * kSplitTP + (READ_BR ? br3(i) : i)];
+    __syncwarp();
+}
+
+template <bool CHAIN>
+__global__ void __launch_bounds__(32 * kSplitWarps) cdc_split_kernel(const DevFrame *__restrict__ frames,
+                                                                    const int4 *__restrict__ items, int n_items) {
+    __shared__ int32_t smem[kSplitWarps * kSplitWarpWords];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane >> 3, t = lane & 7;                 // block of the warp, thread of the block
+    int32_t *TU = smem + warp * kSplitWarpWords + q * 2 * 8 * kSplitTP, *TV = TU + 8 * kSplitTP;
+    // twiddles alpha^(t br3(i)) (forward, step B) and alpha^(-n t) (inverse, step B)
+    int32_t tw1[8], tw2[8];
+    {
+        int64_t a = 1, ai = 1;
+        for (int i = 0; i < t; ++i) {
+            a = a * kAlpha % kF;
+            ai = ai * zinv(kAlpha) % kF;
+        }
+        int64_t pw[8], pwi = 1;
+        pw[0] = 1;
+#pragma unroll
+        for (int i = 1; i < 8; ++i) pw[i] = pw[i - 1] * a % kF;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            tw1[i] = centred64(pw[br3(i)]);
+            tw2[i] = centred64(pwi);
+            pwi = pwi * ai % kF;
+        }
+    }
+    const int wpg = gridDim.x * kSplitWarps;
+    for (int w = blockIdx.x * kSplitWarps + warp; w < n_items * kSplitWarpsPerItem; w += wpg) {
+        const int4 item = items[w / kSplitWarpsPerItem];
+        const int lb = kSplitBlocksPerWarp * (w % kSplitWarpsPerItem) + q;   // block within the item
+        const DevFrame &fr = frames[item.x];
+        const int S = fr.S, npol = fr.n_pol;
+        const int64_t n = fr.n;
+        const bool active = lb < item.z;
+        const int64_t b = (int64_t)item.y + lb;
+        const int64_t base = b * S - (kN - S);
+        // tap spectra in this thread's order: register i is frequency t + 8 br3(i),
+        // stored by cdc_spectra_kernel at index bitrev_6(k)
+        int32_t hu[8], hv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = t + 8 * br3(i);
+            const int idx = (int)(__brev((unsigned)k) >> 26);
+            hu[i] = fr.hspec[idx];
+            hv[i] = fr.hspec[kN + idx];
+        }
+        const int p_first = item.w == 2 ? 0 : item.w, p_end = item.w == 2 ? 2 : item.w + 1;
+        for (int pol = p_first; pol < p_end; ++pol) {
+            int32_t U[8], V[8];
+#pragma unroll
+            for (int j1 = 0; j1 < 8; ++j1) {
+                const int64_t sidx = base + 8 * j1 + t;
+                int32_t re = 0, im = 0;
+                if (active && sidx >= 0 && sidx < n) {
+                    const int8_t *px = fr.in + (sidx * npol + pol) * 2;
+                    re = px[0];
+                    im = px[1];
+                }
+                U[j1] = re + 256 * im;
+                V[j1] = re - 256 * im;
+            }
+            // forward: step A over j1, B and C, D over j2 -> X[t + 8 br3(i)]
+            fnt_fwd<8, kBeta, 13>(U);
+            fnt_fwd<8, kBeta, 13>(V);
+            split_exchange<true, false>(U, tw1, TU, t);
+            split_exchange<true, false>(V, tw1, TV, t);
+            fnt_fwd<8, kBeta, 17>(U);
+            fnt_fwd<8, kBeta, 17>(V);
+            // products with the tap spectra and eqs. (7)/(8)
+            const ZArith za;
+            spectral_products(za, U, hu);
+            spectral_products(za, V, hv);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int32_t a = U[i] + V[i], c = U[i] - V[i];
+                U[i] = rho(a);
+                V[i] = za.mulpow2(c, -256);
+            }
+            // inverse: step A over k2 (bit-reversed input), B and C, D over k1 -> z[t + 8 n1]
+            fnt_inv<8, kBeta, 17>(U);
+            fnt_inv<8, kBeta, 17>(V);
+            split_exchange<false, true>(U, tw2, TU, t);
+            split_exchange<false, true>(V, tw2, TV, t);
+            fnt_inv<8, kBeta, 17>(U);
+            fnt_inv<8, kBeta, 17>(V);
+            if (!active) continue;
+            // |z| <= 31 * 1024 < 32767, so the centred residue is the value
+#pragma unroll
+            for (int n1 = 0; n1 < 8; ++n1) {
+                const int pos = t + 8 * n1;
+                if (pos < kN - S) continue;
+                const int64_t so = b * S + pos - (kN - S);
+                if (so >= n) continue;
+                const int32_t re = rhoc(U[n1]), im = rhoc(V[n1]);
+                if (!CHAIN) {
+                    ((uint32_t *)fr.out)[so * npol + pol] = ((uint32_t)re & 0xFFFFu) | ((uint32_t)im << 16);
+                } else if (((so - fr.phase) & 1) == 0 && so >= fr.phase) {
+                    const int sft = fr.shift;
+                    const int32_t rnd = sft > 0 ? (1 << (sft - 1)) : 0;
+                    const uint32_t qv = (uint32_t)(sat5((re + rnd) >> sft) & 0xFF) |
+                                        ((uint32_t)(sat5((im + rnd) >> sft) & 0xFF) << 8);
+                    ((uint16_t *)fr.aeq_in)[2 * ((so - fr.phase) >> 1) + pol] = (uint16_t)qv;
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 size_t cdc_smem_bytes(int warps) { return (size_t)warps * kWarpWords * sizeof(uint32_t); }
@@ -286,8 +446,17 @@ cudaError_t cdc_spectra_launch(const DevFrame *frames, int n_frames, cudaStream_
 }
 
 cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, bool both, int warps,
-                       int grid, cudaStream_t stream) {
+                       int grid, cudaStream_t stream, bool split) {
     if (n_items <= 0) return cudaSuccess;
+    if (split) {
+        const int sgrid = (int)std::min<int64_t>(((int64_t)n_items * kSplitWarpsPerItem + kSplitWarps - 1) / kSplitWarps,
+                                                 1 << 20);
+        if (chain)
+            cdc_split_kernel<true><<<sgrid, 32 * kSplitWarps, 0, stream>>>(frames, items, n_items);
+        else
+            cdc_split_kernel<false><<<sgrid, 32 * kSplitWarps, 0, stream>>>(frames, items, n_items);
+        return cudaGetLastError();
+    }
     const dim3 block(32 * warps);
     const size_t smem = cdc_smem_bytes(warps);
     if (chain && both)

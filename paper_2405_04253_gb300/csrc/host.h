@@ -23,6 +23,7 @@ struct fnt_plan {
     int cdc_pols_per_item = 0;   // CDC items: 0 auto, 1 one polarisation, 2 both
     int aeq_occupancy = 0;       // AEQ warps per SM cap (0: as many as resources allow)
     int aeq_kernel = 0;          // AEQ kernel: 0 auto, 1 a warp per chain, 2 a CTA per chain
+    int cdc_kernel = 0;          // CDC kernel: 0 auto, 1 a block per lane, 2 a block per 8 threads
     int smem_per_sm = 0;         // the device's shared memory per SM and per-CTA reserve
     int smem_reserved = 0;
     cudaMemPool_t pool = nullptr;  // per-call work memory, kept mapped between calls
@@ -96,7 +97,9 @@ int aeq_mults_per_block(int na);
 cudaError_t cdc_configure();
 cudaError_t cdc_spectra_launch(const DevFrame *frames, int n_frames, cudaStream_t stream);
 cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, bool both, int warps, int grid,
-                       cudaStream_t stream);
+                       cudaStream_t stream, bool split = false);
+// Whether a CDC launch of n_items 32-block items takes the split-block kernel.
+bool cdc_use_split(const fnt_plan *p, int64_t n_items);
 size_t aeq_smem_bytes(int na, int warps, int period);
 cudaError_t aeq_configure();
 cudaError_t aeq_launch(int na, const DevFrame *frames, const AeqChain *chains, int n_chains, AeqParams prm,

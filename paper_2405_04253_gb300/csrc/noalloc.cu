@@ -211,7 +211,7 @@ extern "C" fnt_status fnt_cdc_aeq_run_noalloc(const fnt_plan *p, const fnt_frame
     e = cdc_spectra_launch(frames, 1, stream);
     if (e != cudaSuccess) return cuda_fail(e, "noalloc: tap spectra launch");
     e = cdc_launch(frames, (const int4 *)(base + kOffItems), n_items, true, false, nw,
-                   std::min((n_items + nw - 1) / nw, p->n_sm * 64), stream);
+                   std::min((n_items + nw - 1) / nw, p->n_sm * 64), stream, cdc_use_split(p, n_items));
     if (e != cudaSuccess) return cuda_fail(e, "noalloc: cdc kernel launch");
     if (nc > 0) {
         if (n_chains > 1 && f->aeq_state) {

@@ -36,18 +36,27 @@ CDC_CASES = [(1000, 1, 17), (777, 2, 19), (3000, 2, 5), (64, 1, 17), (47, 2, 17)
              (0, 2, 17), (333, 1, 1), (5000, 2, 31), (48 * 32 * 3 + 7, 2, 17), (20000, 2, 12)]
 
 
+def cdc_plan(cdck, **kw):
+    """CDC kernel 1: a block per lane; 2: a block per 8 threads (four-step)."""
+    plan = F.Plan(**kw)
+    plan.set_cdc_kernel(cdck)
+    return plan
+
+
+@pytest.mark.parametrize("cdck", [1, 2])
 @pytest.mark.parametrize("n,n_pol,L", CDC_CASES)
-def test_cdc_random_matches_oracle(orc, n, n_pol, L):
+def test_cdc_random_matches_oracle(orc, n, n_pol, L, cdck):
     rng = np.random.default_rng(100 + n + L)
     x = rng.integers(-16, 16, (n, n_pol, 2)).astype(np.int8)
     taps = rng.integers(-32, 32, (L, 2)).astype(np.int8)
-    plan = F.Plan()
+    plan = cdc_plan(cdck)
     got = run_cdc(plan, x, taps)
     assert np.array_equal(got, orc.cdc(x, taps) if n else np.zeros((0, n_pol, 2), np.int32))
 
 
+@pytest.mark.parametrize("cdck", [1, 2])
 @pytest.mark.parametrize("step,L", [(32, 17), (40, 17), (48, 17), (32, 31), (34, 31)])
-def test_cdc_custom_step(orc, step, L):
+def test_cdc_custom_step(orc, step, L, cdck):
     """Includes the Tab. 1 operating point: 50 % overlap (S = 32) with up to
     31 taps, worst-case magnitudes included."""
     rng = np.random.default_rng(step + L)
@@ -55,31 +64,34 @@ def test_cdc_custom_step(orc, step, L):
     x[:700] = -16
     taps = rng.integers(-32, 32, (L, 2)).astype(np.int8)
     taps[: L // 2] = -32
-    got = run_cdc(F.Plan(cdc_step=step), x, taps)
+    got = run_cdc(cdc_plan(cdck, cdc_step=step), x, taps)
     assert np.array_equal(got, orc.cdc(x, taps, 64, 4080, step))
 
 
-def test_cdc_extremes(orc):
+@pytest.mark.parametrize("cdck", [1, 2])
+def test_cdc_extremes(orc, cdck):
     n = 4096
     for xv, hv in [(-16, -32), (15, 31), (-16, 31), (-1, -1)]:
         x = np.full((n, 2, 2), xv, dtype=np.int8)
         x[::7, 1, 0] = -xv - 1 if xv < 15 else -16
         taps = np.full((31, 2), hv, dtype=np.int8)
-        got = run_cdc(F.Plan(), x, taps)
+        got = run_cdc(cdc_plan(cdck), x, taps)
         assert np.array_equal(got, orc.cdc(x, taps))
 
 
-def test_cdc_synthetic_config1(orc):
+@pytest.mark.parametrize("cdck", [0, 1, 2])
+def test_cdc_synthetic_config1(orc, cdck):
     f = synth.config1()
-    got = run_cdc(F.Plan(), f.x, f.taps)
+    got = run_cdc(cdc_plan(cdck), f.x, f.taps)
     assert np.array_equal(got, orc.cdc(f.x, f.taps))
 
 
+@pytest.mark.parametrize("cdck", [1, 2])
 @pytest.mark.parametrize("pols", [0, 1, 2])
-def test_cdc_batch_of_mixed_frames(orc, pols):
+def test_cdc_batch_of_mixed_frames(orc, pols, cdck):
     """Items of one or of both polarisations (single-pol frames always take one)."""
     rng = np.random.default_rng(77)
-    plan = F.Plan()
+    plan = cdc_plan(cdck)
     plan.set_cdc_items(pols)
     frames, refs = [], []
     for i in range(9):
@@ -333,9 +345,10 @@ def oracle_chain(orc, x, taps, **kw):
 
 
 @pytest.mark.parametrize("na,alpha", [(32, 2), (64, 4080)])
-def test_chain_synthetic_matches_oracle(orc, na, alpha):
+@pytest.mark.parametrize("cdck", [1, 2])
+def test_chain_synthetic_matches_oracle(orc, na, alpha, cdck):
     f = synth.config2(1 << 12)
-    plan = F.Plan(n_aeq=na, alpha_aeq=alpha, mu_shift=9)
+    plan = cdc_plan(cdck, n_aeq=na, alpha_aeq=alpha, mu_shift=9)
     nsym = F.chain_nsym(f.x.shape[0], f.taps.shape[0])
     out = i16((nsym, 4))
     st = dev(np.zeros((4, 4, 16), np.int32))

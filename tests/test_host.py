@@ -266,6 +266,7 @@ def test_every_entry_point_rejects_null_handles_without_gpu():
         "fnt_plan_set_pipeline": (None, 1),
         "fnt_plan_set_aeq_occupancy": (None, 8),
         "fnt_plan_set_aeq_kernel": (None, 2),
+        "fnt_plan_set_cdc_kernel": (None, 2),
         "fnt_plan_initial_taps": (None, None),
         "fnt_plan_set_cdc_items": (None, 0),
         "fnt_plan_set_tensor_gradient": (None, 0),
