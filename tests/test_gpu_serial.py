@@ -148,3 +148,21 @@ def test_prepared_graph_batch_serial_stream_carries_taps(orc):
         ref, T = orc.chain(f.x, f.taps, orc.ChainParams(**kw), T0=T)
         assert np.array_equal(out.cpu().numpy(), ref)
         assert np.array_equal(st.cpu().numpy(), T)
+
+
+def test_automatic_kernel_choices():
+    """The automatic choices the launches make (results never depend on them):
+    the CTA-per-chain AEQ for few long chains only, never with summation in
+    Z_F; the split-block CDC below two 32-block items per SM."""
+    p = F.Plan(n_aeq=64, alpha_aeq=4080)
+    assert p.aeq_kernel_for(1, 1 << 20) == 2                 # one long stream
+    assert p.aeq_kernel_for(76, 256 * 48) == 2               # 152 items, 256 blocks
+    assert p.aeq_kernel_for(76, 256 * 48 - 48) == 1          # 255 blocks: short chains
+    assert p.aeq_kernel_for(77, 1 << 20) == 1                # more items than SMs
+    p.set_aeq_kernel(1)
+    assert p.aeq_kernel_for(1, 1 << 20) == 1
+    p.set_aeq_kernel(2)
+    assert p.aeq_kernel_for(1000, 16) == 2
+    fs = F.Plan(aeq_freq_sum=2)
+    fs.set_aeq_kernel(2)
+    assert fs.aeq_kernel_for(1, 1 << 20) == 1                # summation lives in the warp kernel
