@@ -703,14 +703,21 @@ def run_cfg1(args):
     per = sorted(e[0].elapsed_time(e[1]) for e in evs)
     ms = statistics.mean(per)
     ops = cdc_ops(n, 48, n_pol=1)
+    n_items = math.ceil(math.ceil(n / 48) / 32)
+    split = plan.cdc_kernel_for(n_items) == 2
+    kname = "cdc_split_kernel<cdc>" if split else "cdc_kernel<cdc>"
+    src = source_hash("cdc.cu", "zf.cuh", "internal.h")
     return {"workload": "cfg1: single-pol FNT-CDC, 65,536 samples, 17 taps, N=64 alpha=4080 S=48",
             "metric": "Msamples/s", "value": round(n / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
             "steps": args.steps, "gpu_launches_per_step": b.kernel_count(),
             "repeat": {"launches": len(per), "best_ms": round(per[0], 4), "median_ms": round(statistics.median(per), 4)},
-            "roofline": {"bound": "alu", "kernel": "cdc_kernel<cdc>", "achieved": round(ops / (ms * 1e-3) / 1e12, 3),
+            "roofline": {"bound": "alu", "kernel": kname, "achieved": round(ops / (ms * 1e-3) / 1e12, 3),
                          "peak": round(alu_peak_ops() / 1e12, 2), "unit": "Tops/s (int32, algorithmic)",
-                         "frac": round(ops / (ms * 1e-3) / alu_peak_ops(), 4)},
-            "note": "65,536 samples is 1366 blocks: one partial wave of 43 CTAs on 152 SMs, launch-latency bound"}
+                         "frac": round(ops / (ms * 1e-3) / alu_peak_ops(), 4),
+                         "traffic": profiled_traffic(kname, src), "ncu": profiled_counters(kname, src),
+                         "timing": "graph launch included"},
+            "note": "65,536 samples is 1366 blocks in 43 work items of 32 blocks: " +
+                    ("a block per 8 threads, 344 warps" if split else "a block per lane, 43 warps")}
 
 
 def run_cfg3(args):

@@ -337,6 +337,11 @@ FNT_API fnt_status fnt_plan_set_aeq_kernel(fnt_plan *plan, int32_t kind);
  * outside [0, 2]. */
 FNT_API fnt_status fnt_plan_set_cdc_kernel(fnt_plan *plan, int32_t kind);
 
+/* The CDC kernel (1 or 2, as above) a launch of `n_items` CDC work items (32
+ * overlap-save blocks of one polarisation, or of both) of this plan takes; 0
+ * for a null plan. */
+FNT_API int32_t fnt_plan_cdc_kernel_for(const fnt_plan *plan, int64_t n_items);
+
 /* The AEQ kernel (1 or 2, as above) a launch of `n_chains` AEQ chains of this
  * plan, the longest of `longest_symbols` symbols, takes; 0 for a null plan.
  * A chain is a frame, or one AEQ segment of a frame with its warm-up. */

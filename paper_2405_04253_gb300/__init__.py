@@ -90,6 +90,7 @@ SIGNATURES = {
     "fnt_plan_set_aeq_occupancy": (_I32, [_VP, _I32]),
     "fnt_plan_set_aeq_kernel": (_I32, [_VP, _I32]),
     "fnt_plan_set_cdc_kernel": (_I32, [_VP, _I32]),
+    "fnt_plan_cdc_kernel_for": (_I32, [_VP, _I64]),
     "fnt_plan_aeq_kernel_for": (_I32, [_VP, _I64, _I64]),
     "fnt_op_counts_for": (_I32, [ctypes.POINTER(PlanDesc), _I32, ctypes.POINTER(OpCounts)]),
     "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
@@ -216,6 +217,10 @@ class Plan:
         """CDC kernel: 1 a block per lane, 2 a block per 8 threads, 0
         automatic; same results."""
         check(lib().fnt_plan_set_cdc_kernel(self.handle, int(kind)))
+
+    def cdc_kernel_for(self, n_items: int) -> int:
+        """The CDC kernel (1 or 2) a launch of n_items 32-block work items takes."""
+        return int(lib().fnt_plan_cdc_kernel_for(self.handle, int(n_items)))
 
     def aeq_kernel_for(self, n_chains: int, longest_symbols: int) -> int:
         """The AEQ kernel (1 or 2) a launch of n_chains chains, the longest of

@@ -284,6 +284,11 @@ bool fnt::cdc_use_split(const fnt_plan *p, int64_t n_items) {
     return n_items < 2 * (int64_t)p->n_sm;
 }
 
+extern "C" int32_t fnt_plan_cdc_kernel_for(const fnt_plan *p, int64_t n_items) {
+    if (!p) return 0;
+    return cdc_use_split(p, n_items) ? 2 : 1;
+}
+
 extern "C" int32_t fnt_plan_aeq_kernel_for(const fnt_plan *p, int64_t n_chains, int64_t longest_symbols) {
     if (!p) return 0;
     return aeq_use_serial(p, n_chains, longest_symbols) ? 2 : 1;

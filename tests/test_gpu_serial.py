@@ -166,3 +166,7 @@ def test_automatic_kernel_choices():
     fs = F.Plan(aeq_freq_sum=2)
     fs.set_aeq_kernel(2)
     assert fs.aeq_kernel_for(1, 1 << 20) == 1                # summation lives in the warp kernel
+    c = F.Plan()
+    assert c.cdc_kernel_for(43) == 2 and c.cdc_kernel_for(303) == 2 and c.cdc_kernel_for(304) == 1
+    c.set_cdc_kernel(1)
+    assert c.cdc_kernel_for(1) == 1

@@ -288,12 +288,13 @@ def test_every_entry_point_rejects_null_handles_without_gpu():
         assert getattr(L, name)(None) == fnt.FNT_OK, name
     assert L.fnt_batch_kernel_count(None) == 0
     assert L.fnt_plan_aeq_kernel_for(None, 1, 1 << 20) == 0
+    assert L.fnt_plan_cdc_kernel_for(None, 1) == 0
     assert L.fnt_session_pending(None) == 0
     assert fnt.last_error()                  # the last failure left its text
     decl = set(header_functions())
     covered = set(calls) | {"fnt_plan_destroy", "fnt_batch_destroy", "fnt_session_destroy", "fnt_batch_kernel_count",
                             "fnt_session_pending", "fnt_last_error", "fnt_version", "fnt_plan_desc_default",
-                            "fnt_plan_aeq_kernel_for"}
+                            "fnt_plan_aeq_kernel_for", "fnt_plan_cdc_kernel_for"}
     assert decl <= covered, decl - covered
 
 
