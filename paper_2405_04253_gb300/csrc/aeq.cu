@@ -141,8 +141,10 @@ struct SplitInput {
 //   JoinDiff, n' in [0, K): only the difference is kept; lane 0 forms it for
 //     n' = j and lane 1 for n' = j + K/2 (j < K/2), one exchange serving both.
 // Every lane thus produces (N - K)/2 outputs and no discarded one.  Each
-// output v (|true value| <= 32512) is stored as v * wgt, decoded first (DEC)
-// when the inputs were summed in Z_F.
+// output v (|true value| <= 32512) is stored as it is; when the inputs were
+// summed in Z_F (DEC) it is decoded first and masked by wgt (0 for all but the
+// first input lane).  The tap-group weights 128 / 1 are applied where the
+// outputs are summed.
 template <bool DEC>
 __device__ __forceinline__ int32_t join_value(int32_t v) {
     v = rhoc(v);
@@ -155,7 +157,8 @@ struct JoinBoth {
         constexpr int32_t W = TwTab<NA, AINV>::tab.w[J];
         const int32_t t = odd ? mulb<18, W>(x[J]) : x[J];         // lane 1 sends alpha^-n' E1[n']
         const int32_t r = __shfl_xor_sync(0xffffffffu, t, 1);
-        row[J] = join_value<DEC>(odd ? r - t : t + r) * wgt;
+        const int32_t v = join_value<DEC>(odd ? r - t : t + r);
+        row[J] = DEC ? v * wgt : v;
         if constexpr (J + 1 < NA / 2) JoinBoth<NA, AINV, DEC, J + 1>::run(x, row, wgt, odd);
     }
 };
@@ -170,7 +173,8 @@ struct JoinDiff {
         const int32_t send = odd ? mulb<18, WA>(x[J]) : x[J + H];
         const int32_t own = odd ? mulb<18, WB>(x[J + H]) : x[J];
         const int32_t r = __shfl_xor_sync(0xffffffffu, send, 1);
-        row[J] = join_value<DEC>(odd ? r - own : own - r) * wgt;
+        const int32_t v = join_value<DEC>(odd ? r - own : own - r);
+        row[J] = DEC ? v * wgt : v;
         if constexpr (J + 1 < H) JoinDiff<NA, AINV, DEC, J + 1>::run(x, row, wgt, odd);
     }
 };
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                 for (int j = 0; j < M; ++j) y[j] = wcache[32 * j];
             }
             const int32_t *xrow = xf + (bb * 4 + s1) * C::XF_ROW + h * C::HALF;
-            spectral_products(ZArith{}, y, xrow);
+            spectral_products(RedArith{}, y, xrow);
             if (FS && fsum) {
                 // frequency-domain summation: the four input lanes of an (output,
                 // group, half) all hold the sum of their products in Z_F
@@ -448,13 +452,12 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                 if (FS && fsum) {
                     // a summed output may exceed the per-pair bound (and wraps with
                     // freq_sum = 1): the exact signed decode of the residue
-                    const int32_t wgt = s1 != 0 ? 0 : (g ? 1 : 128);
+                    const int32_t wgt = s1 != 0 ? 0 : 1;
                     if constexpr (M > K) JoinBoth<NA, C::AINV, true, K>::run(y, rrow - K + (odd ? M : 0), wgt, odd);
                     JoinDiff<NA, C::AINV, true, 0>::run(y, rrow + (M - K) + (odd ? K / 2 : 0), wgt, odd);
                 } else {
-                    const int32_t wgt = g ? 1 : 128;
-                    if constexpr (M > K) JoinBoth<NA, C::AINV, false, K>::run(y, rrow - K + (odd ? M : 0), wgt, odd);
-                    JoinDiff<NA, C::AINV, false, 0>::run(y, rrow + (M - K) + (odd ? K / 2 : 0), wgt, odd);
+                    if constexpr (M > K) JoinBoth<NA, C::AINV, false, K>::run(y, rrow - K + (odd ? M : 0), 1, odd);
+                    JoinDiff<NA, C::AINV, false, 0>::run(y, rrow + (M - K) + (odd ? K / 2 : 0), 1, odd);
                 }
             }
             __syncwarp();
@@ -465,8 +468,9 @@ __global__ void __launch_bounds__(128) aeq_kernel(const DevFrame *__restrict__ f
                 int32_t a0 = 0, a1 = 0;
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
-                    a0 += red[m * C::RED_ROW + i];
-                    a1 += red[(8 + m) * C::RED_ROW + i];
+                    // task row m = 2 s1 + g: the hi group (g = 0) weighs 128
+                    a0 += (m & 1 ? 1 : 128) * red[m * C::RED_ROW + i];
+                    a1 += (m & 1 ? 1 : 128) * red[(8 + m) * C::RED_ROW + i];
                 }
                 const int32_t z0 = min(max(a0 >> 7, -32768), 32767);
                 const int32_t z1 = min(max(a1 >> 7, -32768), 32767);

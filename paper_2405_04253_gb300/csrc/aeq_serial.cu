@@ -102,23 +102,8 @@ __device__ __forceinline__ void cp_async4s(uint32_t *smem, const uint32_t *gmem,
 
 __device__ __forceinline__ void cp_async_wait_alls() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// a b (mod F) as a lazy residue (|result| < 2^17) for |a| < 2^18, |b| <= 2^15 + 8:
-// the 64-bit product is hi 2^32 + lo with 2^32 = 1 (mod F), and lo = l1 2^16 + l0
-// with 2^16 = -1, so a b = hi + l0 - l1 (mod F).
-__device__ __forceinline__ int32_t mulred(int32_t a, int32_t b) {
-    const int64_t t = (int64_t)a * b;
-    const uint32_t lo = (uint32_t)t;
-    return (int32_t)(t >> 32) + (int32_t)(lo & 0xFFFFu) - (int32_t)(lo >> 16);
-}
-
-// The Z_F arithmetic of this kernel's product stage (64-bit product reduced
-// by mulred), as a policy so that the host can count the products.
-struct RedArith {
-    __device__ __forceinline__ int32_t mulmod(int32_t a, int32_t h) const { return mulred(a, h); }
-};
-
 // One thread's piece of a pointwise product: u[i] <- u[i] X_in[i], the input
-// spectrum row read 16 bytes at a time.
+// spectrum row read 16 bytes at a time (RedArith in the kernel).
 template <class A, int NP>
 FNT_HD void piece_products(const A &ar, int32_t (&u)[NP], const int32_t *xrow) {
 #pragma unroll

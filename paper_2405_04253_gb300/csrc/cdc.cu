@@ -276,14 +276,6 @@ constexpr int64_t kBeta = zpow(kAlpha, 8);                 // order 8
 
 __device__ __forceinline__ int br3(int i) { return ((i & 1) << 2) | (i & 2) | ((i >> 2) & 1); }
 
-// a b (mod F) as a lazy residue for |a| < 2^18, |b| <= 2^15 + 8: the 64-bit
-// product is hi 2^32 + lo with 2^32 = 1 and 2^16 = -1 (mod F).
-__device__ __forceinline__ int32_t mulred64(int32_t a, int32_t b) {
-    const int64_t t = (int64_t)a * b;
-    const uint32_t lo = (uint32_t)t;
-    return (int32_t)(t >> 32) + (int32_t)(lo & 0xFFFFu) - (int32_t)(lo >> 16);
-}
-
 __device__ __forceinline__ int32_t centred64(int64_t v) {
     v %= kF;
     if (v < 0) v += kF;
@@ -297,7 +289,7 @@ __device__ __forceinline__ int32_t centred64(int64_t v) {
 template <bool ROW_BR, bool READ_BR>
 __device__ __forceinline__ void split_exchange(int32_t (&x)[8], const int32_t (&tw)[8], int32_t *T, int t) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) T[(ROW_BR ? br3(i) : i) * kSplitTP + t] = mulred64(x[i], tw[i]);   // < 2^17
+    for (int i = 0; i < 8; ++i) T[(ROW_BR ? br3(i) : i) * kSplitTP + t] = mulred(x[i], tw[i]);   // < 2^17
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < 8; ++i) x[i] = T[t * kSplitTP + (READ_BR ? br3(i) : i)];

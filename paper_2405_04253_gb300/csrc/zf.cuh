@@ -112,6 +112,22 @@ struct ZArith {
     FNT_HD int32_t mulpow2(int32_t a, int32_t c) const { return rho(a * c); }         // |a c| < 2^31
 };
 
+// a b (mod F) as a lazy residue (|result| < 2^17) for |a| < 2^18, |b| <= 2^15 + 8:
+// the 64-bit product is hi 2^32 + lo with 2^32 = 1 (mod F), and lo = l1 2^16 + l0
+// with 2^16 = -1, so a b = hi + l0 - l1 (mod F).  Four instructions where
+// rho(rhoc(a) b) takes six.
+FNT_HD int32_t mulred(int32_t a, int32_t b) {
+    const int64_t t = (int64_t)a * b;
+    const uint32_t lo = (uint32_t)t;
+    return (int32_t)(t >> 32) + (int32_t)(lo & 0xFFFFu) - (int32_t)(lo >> 16);
+}
+
+// The same products through mulred (operands within mulred's bounds).
+struct RedArith {
+    FNT_HD int32_t mulmod(int32_t a, int32_t h) const { return mulred(a, h); }
+    FNT_HD int32_t mulpow2(int32_t a, int32_t c) const { return rho(a * c); }
+};
+
 // Host policy that counts, instead of computing: general products in *mults,
 // power-of-two multiplications in *shifts.
 struct CountArith {
