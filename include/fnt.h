@@ -337,6 +337,28 @@ FNT_API fnt_status fnt_plan_set_aeq_kernel(fnt_plan *plan, int32_t kind);
  * outside [0, 2]. */
 FNT_API fnt_status fnt_plan_set_cdc_kernel(fnt_plan *plan, int32_t kind);
 
+/* The one-block-per-lane CDC kernel fetches the 32 input windows of a PDM work
+ * item of one polarisation (items of both polarisations use 4-byte copies),
+ * one contiguous span of the frame, with a single TMA bulk copy
+ * (cp.async.bulk) into shared memory when the span, widened to 16-byte
+ * boundaries, lies inside the frame and the input is 16-byte aligned; other
+ * items use 4-byte asynchronous copies.  The copy's completion is awaited on an
+ * mbarrier for at most about 5 ms.  A wait that runs out sets bit 1
+ * (FNT_FAULT_CDC_WINDOW_WAIT) of the current device's fault word, and that
+ * warp stops (its blocks' outputs are not written); nothing else waits on the
+ * device.  fnt_device_faults returns the fault word of the current device and,
+ * with clear != 0, resets it.  Errors: FNT_ERR_INVALID (null faults),
+ * FNT_ERR_CUDA. */
+#define FNT_FAULT_CDC_WINDOW_WAIT 1u
+FNT_API fnt_status fnt_device_faults(int32_t clear, uint32_t *faults);
+
+/* Test hook: with mode 1, later one-shot calls and prepared batches of this
+ * plan arm the CDC's window barrier without issuing the bulk copy, so the
+ * bounded wait runs out and sets FNT_FAULT_CDC_WINDOW_WAIT: a way to test that
+ * path without faulting anything.  0 (default) is normal operation.
+ * FNT_ERR_INVALID for other modes. */
+FNT_API fnt_status fnt_plan_set_test_inject(fnt_plan *plan, int32_t mode);
+
 /* The CDC kernel (1 or 2, as above) a launch of `n_items` CDC work items (32
  * overlap-save blocks of one polarisation, or of both) of this plan takes; 0
  * for a null plan. */

@@ -91,6 +91,8 @@ SIGNATURES = {
     "fnt_plan_set_aeq_kernel": (_I32, [_VP, _I32]),
     "fnt_plan_set_cdc_kernel": (_I32, [_VP, _I32]),
     "fnt_plan_cdc_kernel_for": (_I32, [_VP, _I64]),
+    "fnt_plan_set_test_inject": (_I32, [_VP, _I32]),
+    "fnt_device_faults": (_I32, [_I32, ctypes.POINTER(ctypes.c_uint32)]),
     "fnt_plan_aeq_kernel_for": (_I32, [_VP, _I64, _I64]),
     "fnt_op_counts_for": (_I32, [ctypes.POINTER(PlanDesc), _I32, ctypes.POINTER(OpCounts)]),
     "fnt_cdc_run": (_I32, [_VP, ctypes.POINTER(BatchC), _VP]),
@@ -132,6 +134,16 @@ def lib(path: str | None = None):
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+FAULT_CDC_WINDOW_WAIT = 1
+
+
+def device_faults(clear: bool = False) -> int:
+    """The current device's fault word (bits set by bounded waits that ran out)."""
+    v = ctypes.c_uint32()
+    check(lib().fnt_device_faults(int(bool(clear)), ctypes.byref(v)))
+    return int(v.value)
 
 
 def last_error() -> str:
@@ -217,6 +229,11 @@ class Plan:
         """CDC kernel: 1 a block per lane, 2 a block per 8 threads, 0
         automatic; same results."""
         check(lib().fnt_plan_set_cdc_kernel(self.handle, int(kind)))
+
+    def set_test_inject(self, mode: int):
+        """Test hook: 1 makes the CDC's bulk-copy window waits run out (see
+        fnt_plan_set_test_inject); 0 is normal operation."""
+        check(lib().fnt_plan_set_test_inject(self.handle, int(mode)))
 
     def cdc_kernel_for(self, n_items: int) -> int:
         """The CDC kernel (1 or 2) a launch of n_items 32-block work items takes."""

@@ -284,6 +284,22 @@ bool fnt::cdc_use_split(const fnt_plan *p, int64_t n_items) {
     return n_items < 2 * (int64_t)p->n_sm;
 }
 
+extern "C" fnt_status fnt_plan_set_test_inject(fnt_plan *p, int32_t mode) {
+    if (!p) return fail(FNT_ERR_INVALID, "null plan");
+    if (mode != 0 && mode != 1) return fail(FNT_ERR_INVALID, "test inject mode must be 0 or 1");
+    p->test_inject = mode;
+    return FNT_OK;
+}
+
+extern "C" fnt_status fnt_device_faults(int32_t clear, uint32_t *faults) {
+    if (!faults) return fail(FNT_ERR_INVALID, "null argument");
+    unsigned v = 0;
+    cudaError_t e = cdc_read_faults(&v, clear != 0);
+    if (e != cudaSuccess) return cuda_fail(e, "fnt_device_faults");
+    *faults = v;
+    return FNT_OK;
+}
+
 extern "C" int32_t fnt_plan_cdc_kernel_for(const fnt_plan *p, int64_t n_items) {
     if (!p) return 0;
     return cdc_use_split(p, n_items) ? 2 : 1;
@@ -364,6 +380,7 @@ static fnt_status make_frame(const fnt_plan *p, const fnt_frame &f, int op, int 
     df.out = f.out;
     df.state = f.aeq_state;
     df.n = f.n;
+    df.flags = p->test_inject;
     if (op == FNT_OP_AEQ) {
         df.n_pol = 2;
         df.n_sym = f.n;

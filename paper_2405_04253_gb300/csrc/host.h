@@ -24,6 +24,7 @@ struct fnt_plan {
     int aeq_occupancy = 0;       // AEQ warps per SM cap (0: as many as resources allow)
     int aeq_kernel = 0;          // AEQ kernel: 0 auto, 1 a warp per chain, 2 a CTA per chain
     int cdc_kernel = 0;          // CDC kernel: 0 auto, 1 a block per lane, 2 a block per 8 threads
+    int test_inject = 0;         // DevFrame::flags of the one-shot calls and batches (test hook)
     int smem_per_sm = 0;         // the device's shared memory per SM and per-CTA reserve
     int smem_reserved = 0;
     cudaMemPool_t pool = nullptr;  // per-call work memory, kept mapped between calls
@@ -95,6 +96,7 @@ int cdc_mults_per_block();
 int cdc_butterflies_per_block();
 int aeq_mults_per_block(int na);
 cudaError_t cdc_configure();
+cudaError_t cdc_read_faults(unsigned *faults, bool clear);   // the current device's fault word
 cudaError_t cdc_spectra_launch(const DevFrame *frames, int n_frames, cudaStream_t stream);
 cudaError_t cdc_launch(const DevFrame *frames, const int4 *items, int n_items, bool chain, bool both, int warps, int grid,
                        cudaStream_t stream, bool split = false);

@@ -26,7 +26,7 @@ struct alignas(16) DevFrame {
     int32_t S;             // CDC overlap-save step
     int32_t shift;         // CDC -> AEQ requantisation shift s_c
     int32_t phase;         // decimation phase
-    int32_t pad0;
+    int32_t flags;         // kFrameInjectTmaTimeout: test hook (the CDC's bulk-copy waits run out)
     int32_t *hspec;        // CDC tap spectra H_u [64], H_v [64] (cdc_spectra_kernel writes them)
     int8_t taps[64];       // [L][2] (re, im), zero beyond L
 };
@@ -56,5 +56,11 @@ struct AeqParams {
 };
 
 constexpr int kMaxUpdatePeriod = 64;   // keeps the summed int64 gradient exact
+
+// DevFrame::flags
+constexpr int32_t kFrameInjectTmaTimeout = 1;   // arm the CDC's window barrier without issuing its copy
+
+// Device fault word (fnt_device_faults): bits set by kernels whose bounded waits ran out.
+constexpr unsigned kFaultCdcWindowWait = 1u;
 
 }  // namespace fnt

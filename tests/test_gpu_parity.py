@@ -109,6 +109,28 @@ def test_cdc_batch_of_mixed_frames(orc, pols, cdck):
         assert np.array_equal(fr.out.cpu().numpy().astype(np.int32), ref)
 
 
+def test_cdc_window_bulk_copy_and_its_bounded_wait(orc):
+    """The one-block-per-lane CDC fetches a PDM item's windows with one TMA
+    bulk copy: bit-exact, no fault recorded.  With the test hook the copy is
+    armed but never issued: the bounded wait runs out, the device fault word
+    records it, and the next normal call is exact again."""
+    rng = np.random.default_rng(91)
+    n = 48 * 32 * 20 + 77
+    x = rng.integers(-16, 16, (n, 2, 2)).astype(np.int8)
+    taps = rng.integers(-32, 32, (17, 2)).astype(np.int8)
+    ref = orc.cdc(x, taps)
+    F.device_faults(clear=True)
+    assert np.array_equal(run_cdc(cdc_plan(1), x, taps), ref)
+    assert F.device_faults() == 0
+    bad = cdc_plan(1)
+    bad.set_test_inject(1)
+    run_cdc(bad, x, taps)
+    assert F.device_faults(clear=True) & F.FAULT_CDC_WINDOW_WAIT
+    assert F.device_faults() == 0
+    assert np.array_equal(run_cdc(cdc_plan(1), x, taps), ref)
+    assert F.device_faults() == 0
+
+
 def test_cdc_rejects_bad_frames():
     plan = F.Plan()
     x = torch.zeros((100, 2, 2), dtype=torch.int8, device="cuda")

@@ -267,6 +267,8 @@ def test_every_entry_point_rejects_null_handles_without_gpu():
         "fnt_plan_set_aeq_occupancy": (None, 8),
         "fnt_plan_set_aeq_kernel": (None, 2),
         "fnt_plan_set_cdc_kernel": (None, 2),
+        "fnt_plan_set_test_inject": (None, 1),
+        "fnt_device_faults": (0, None),
         "fnt_plan_initial_taps": (None, None),
         "fnt_plan_set_cdc_items": (None, 0),
         "fnt_plan_set_tensor_gradient": (None, 0),
