@@ -290,6 +290,7 @@ def run_fnt(args, rank, world, local_rank, oracle_pool=None):
         p = fnt.Plan(n_aeq=wl["n_aeq"], alpha_aeq=wl["alpha_aeq"], mu_shift=MU_SHIFT, aeq_segment=segment,
                      aeq_warmup=warmup, aeq_update_period=wl.get("period", 1), aeq_freq_sum=wl.get("freq_sum", 0))
         p.set_tensor_gradient(args.tensor_gradient)
+        p.set_aeq_kernel(args.aeq_kernel)
         return p
 
     plan = make_plan(wl["segment"], wl["warmup"])
@@ -806,7 +807,7 @@ def run_cfg4(args):
     # the serial plan (the paper's update rule over every frame, taps carried
     # from frame to frame of a link) is the headline; the same plan with the
     # warp-per-chain AEQ kernel forced, and a segmented plan, for comparison
-    plans = {"serial": (dict(), 0), "serial_warp_kernel": (dict(), 1),
+    plans = {"serial": (dict(), 0), "serial_cta_kernel": (dict(), 2), "serial_warp_kernel": (dict(), 1),
              "segmented": (dict(aeq_segment=1024, aeq_warmup=0), 0),
              "segmented_warp_kernel": (dict(aeq_segment=1024, aeq_warmup=0), 1)}
     if args.cfg4_plans:
@@ -885,7 +886,7 @@ def run_cfg4(args):
                      "aeq": "one serial run per frame (eq. (6) over the frame)" if not over else
                             f"segments of {over['aeq_segment']} + {over['aeq_warmup']} from the link's taps",
                      "aeq_kernel": {0: "automatic (a CTA per chain when a wave's chains fit one per SM)",
-                                    1: "a warp per chain (forced)"}[kernel]}
+                                    1: "a warp per chain (forced)", 2: "a CTA per chain (forced)"}[kernel]}
     offered_gsps = sum(f.x.shape[0] for f in tr.frames) / tr.frames[-1].arrival_s / 1e9
     return {"workload": f"cfg4: {len(tr.frames)} frames, Poisson 20k frames/s over {len(tr.link_taps)} links, "
                         "2^12..2^16 samples, AEQ N=32 state carried per link, 8 GB cap, pinned host I/O",
@@ -902,13 +903,15 @@ def main(argv=None):
     ap.add_argument("--frames", type=int, default=0, help="cfg3 / cfg4: frame count (default 4096 / 2048)")
     ap.add_argument("--streams", type=int, default=4, help="cfg4: concurrent waves")
     ap.add_argument("--cfg4-plans", default="",
-                    help="cfg4: comma list of plans to run (serial, serial_warp_kernel, segmented, "
+                    help="cfg4: comma list of plans to run (serial, serial_cta_kernel, serial_warp_kernel, segmented, "
                          "segmented_warp_kernel); default all")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-segments", type=int, default=0,
                     help="AEQ segments the CPU-baseline oracle recomputes (0 = all: the whole step)")
     ap.add_argument("--ref-segments", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--aeq-kernel", type=int, default=0, choices=(0, 1, 2),
+                    help="cfg2 / cfg5: AEQ kernel (0 automatic, 1 a warp, 2 a CTA per chain and polarisation)")
     ap.add_argument("--tensor-gradient", action="store_true",
                     help="cfg2 / cfg5: AEQ gradient on the tensor cores (bit-identical; off = integer path)")
     ap.add_argument("--aeq-freq-sum", type=int, default=0, choices=(0, 1, 2),

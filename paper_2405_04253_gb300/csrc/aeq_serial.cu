@@ -21,9 +21,9 @@
 //     The outputs then follow from an R-point transform across the R threads,
 //       c[n' + (N/R) m] = sum_r (alpha^{-N/R})^{m r} v_r[n'],
 //     done in registers after a transpose through shared memory.  Kept outputs
-//     (n >= K) are decoded (exact by constraint (5)), weighted 128 / 1 and
-//     summed over the warp's tasks by shuffles.
-//   phase 2 (SA threads): y summed over the task partials, z = sat16(y >> 7),
+//     (n >= K) are decoded (exact by constraint (5)) and stored per task.
+//   phase 2 (2 SA threads): y summed over the task rows (weights 128 and 1 for
+//     the two tap groups), z = sat16(y >> 7),
 //     the RDE error e of the polarisation; outputs are stored.
 //   phase 3 (256 threads): the gradient of eq. (6), G[f][k] = sum_i e_i z_o,i
 //     x_s1[t0 + i - k], as (filter, 4 taps, 1/8 of the symbols) per thread with
