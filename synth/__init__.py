@@ -107,6 +107,21 @@ def quantize5(v: np.ndarray, rms_lsb: float = 5.0) -> np.ndarray:
 def received(rng: np.random.Generator, n_samples: int, n_pol: int, fiber_km: float,
              snr_db: float, drift_rad_per_s: float = 100.0, chunk: int = 1 << 22) -> np.ndarray:
     """Received 2-sps signal, int8 [n_samples, n_pol, 2] after 5-bit quantisation."""
+    return transmission(rng, n_samples, n_pol, fiber_km, snr_db, drift_rad_per_s, chunk).x
+
+
+@dataclass
+class Transmission:
+    x: np.ndarray          # int8 [n_samples, n_pol, 2]: the received signal after 5-bit quantisation
+    symbols: np.ndarray    # complex128 [n_pol, n_sym]: the transmitted 16QAM symbols (levels +-1, +-3)
+    analog: np.ndarray     # complex128 [n_pol, n_samples]: the received signal before quantisation
+
+
+def transmission(rng: np.random.Generator, n_samples: int, n_pol: int, fiber_km: float,
+                 snr_db: float, drift_rad_per_s: float = 100.0, chunk: int = 1 << 22) -> Transmission:
+    """The transmitted symbols, the received 2-sps signal and its 5-bit
+    quantisation (the same draws as received()).  Symbol j is at sample 2 j of
+    the received signal."""
     n_sym = (n_samples + 1) // 2
     sym = qam16(rng, n_pol, n_sym)
     h = channel_impulse(fiber_km)
@@ -133,7 +148,7 @@ def received(rng: np.random.Generator, n_samples: int, n_pol: int, fiber_km: flo
     sigma = math.sqrt(p_sig / 10 ** (snr_db / 10) / 2)
     sig = sig + sigma * (rng.standard_normal(sig.shape) + 1j * rng.standard_normal(sig.shape))
     q = quantize5(sig)                         # [n_pol, n_samples, 2]
-    return np.ascontiguousarray(np.transpose(q, (1, 0, 2)))
+    return Transmission(np.ascontiguousarray(np.transpose(q, (1, 0, 2))), sym, sig)
 
 
 # ----------------------------------------------------------------- configs -----
