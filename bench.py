@@ -894,8 +894,8 @@ def run_cfg4(args):
 
 
 BER_L = 31             # CD taps of the BER study: the longest the library takes (75 km needs about 36 samples)
-BER_MU_SHIFT = 7       # AEQ step of the BER study (the float receivers' 3e-5 on their scale)
-BER_TAP_INIT = 3072    # AEQ centre spike: output power near the mean of the RDE rings
+BER_MU_SHIFT = 6       # AEQ step of the BER study (about the float receivers' 3e-5 on their scale)
+BER_TAP_INIT = 4096    # AEQ centre spike: output power near the mean of the RDE rings
 BER_FLOAT_MU = 3e-5
 
 

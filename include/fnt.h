@@ -235,8 +235,9 @@ FNT_API fnt_status fnt_aeq_run(const fnt_plan *plan, const fnt_frame_batch *batc
 
 /* The receiver chain of the experimental section: FNT-CDC on both
  * polarisations, requantisation of the CDC output to 5 bits
- * (x = sat[-16,15](floor((z + 2^(s-1)) / 2^s)), s = floor(bitlen(E) / 2),
- * E = sum_k |h[k]|^2), resampling to 1 sample/symbol (times t = phase mod 2),
+ * (x = sat[-16,15](floor((z + 2^(s-1)) / 2^s)), s the smallest shift with
+ * 4^s >= 2 E, E = sum_k |h[k]|^2: the AEQ input keeps at most the CDC input's
+ * loading), resampling to 1 sample/symbol (times t = phase mod 2),
  * then FNT-AEQ.  Errors as fnt_cdc_run. */
 FNT_API fnt_status fnt_cdc_aeq_run(const fnt_plan *plan, const fnt_frame_batch *batch, void *stream);
 

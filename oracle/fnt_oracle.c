@@ -18,6 +18,9 @@
  *   orc_cdc                             pinned (equals exact integer linear
  *                                       convolution, computed by numpy)
  *   orc_requant_decimate                pinned (hand-worked cases)
+ *   orc_cdc_shift                       pinned (hand-worked cases; on the
+ *                                       synthetic 75 km link the AEQ input
+ *                                       stays within the ADC's loading)
  *   orc_aeq, mu = 0                     pinned (equals exact 4x4 integer MIMO
  *                                       convolution, computed by numpy)
  *   orc_aeq, adaptive                   pinned: the one-block gradient against a
@@ -267,16 +270,18 @@ static i64 floor_shift(i64 v, int s) {
 }
 
 
-/* CDC -> AEQ requantisation shift s_c (the paper fixes only the 5-bit AEQ input
- * width): with E = sum_k (h_re[k]^2 + h_im[k]^2), s_c = floor(bitlen(E) / 2), the
- * power of two nearest to the filter's L2 gain, so the CDC output keeps roughly
- * the input's RMS.  bitlen(0) = 0. */
+/* CDC -> AEQ requantisation shift s_c (the paper fixes only the 5-bit signal
+ * width): with E = sum_k (h_re[k]^2 + h_im[k]^2), s_c is the smallest s >= 0
+ * with 4^s >= 2 E, i.e. 2^s >= sqrt(2 E).  CD taps designed for a signal that
+ * fills about half of the sampled band have an in-band gain near sqrt(2 E)
+ * (sqrt(E) is their gain on white input), so the 5-bit AEQ input keeps at
+ * most the 5-bit CDC input's loading and does not saturate.  E = 0 gives 0. */
 int orc_cdc_shift(const int8_t *taps, int L) {
     i64 E = 0;
     for (int k = 0; k < L; ++k) E += (i64)taps[2 * k] * taps[2 * k] + (i64)taps[2 * k + 1] * taps[2 * k + 1];
-    int bl = 0;
-    while (E > 0) { ++bl; E >>= 1; }
-    return bl / 2;
+    int s = 0;
+    while (E > 0 && ((i64)1 << (2 * s)) < 2 * E) ++s;
+    return s;
 }
 
 /* Decimation phase (2 sps -> 1 sps keeps times t = phase mod 2): the parity of

@@ -60,15 +60,16 @@ static bool valid_transform(int64_t N, int64_t alpha) {
     return hmod(N) != 0;
 }
 
+// CDC -> AEQ requantisation shift: the smallest s with 2^(2s) >= 2 E, E the
+// taps' energy.  CD taps have an in-band gain near sqrt(2 E) on a signal that
+// fills about half of the sampled band, so the 5-bit AEQ input keeps at most
+// the 5-bit CDC input's loading and does not saturate.
 int cdc_shift_of(const int8_t *taps, int L) {
     int64_t E = 0;
     for (int k = 0; k < L; ++k) E += (int64_t)taps[2 * k] * taps[2 * k] + (int64_t)taps[2 * k + 1] * taps[2 * k + 1];
-    int bl = 0;
-    while (E > 0) {
-        ++bl;
-        E >>= 1;
-    }
-    return bl / 2;
+    int s = 0;
+    while (E > 0 && (int64_t{1} << (2 * s)) < 2 * E) ++s;
+    return s;
 }
 
 int decim_phase_of(int L) { return ((L - 1) / 2) & 1; }

@@ -91,11 +91,11 @@ def test_snr_at_ber_interpolates_log_linearly():
 def test_integer_chain_converges_on_the_75km_channel(orc):
     """The integer FNT-CDC + FNT-AEQ chain (oracle) with 31 CD taps at 22 dB:
     blind RDE convergence from the centre spike within 2^16 symbols and a BER
-    after it below 2e-2 on both polarisations."""
+    after it below 5e-3 on both polarisations."""
     n_sym = 1 << 17
     tr = synth.transmission(synth.rng_for(6, 0), 2 * n_sym, 2, 75.0, 22.0)
     taps = synth.cd_taps(75.0, 31)
-    out, _ = orc.chain(tr.x, taps, orc.ChainParams(n_aeq=32, alpha_aeq=2, mu_shift=7, w0=3072))
+    out, _ = orc.chain(tr.x, taps, orc.ChainParams(n_aeq=32, alpha_aeq=2, mu_shift=6, w0=4096))
     c = ber.count_errors(ber.chain_to_complex(out), tr.symbols, skip=n_sym // 2)
-    assert c.ber < 2e-2, c
-    assert all(e / nb < 2e-2 for _, _, _, e, nb in c.per_pol), c.per_pol
+    assert c.ber < 5e-3, c
+    assert all(e / nb < 5e-3 for _, _, _, e, nb in c.per_pol), c.per_pol

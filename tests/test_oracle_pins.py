@@ -165,10 +165,32 @@ def test_cdc_alternative_root_same_result(orc):
 # -------------------------------------------------------- requant / resample -----
 
 def test_cdc_shift_and_phase(orc):
-    assert orc.cdc_shift(np.array([[1, 0]], dtype=np.int8)) == 0       # E = 1
-    assert orc.cdc_shift(np.array([[3, 4]], dtype=np.int8)) == 2       # E = 25, 5 bits
-    assert orc.cdc_shift(np.array([[31, 31]] * 17, dtype=np.int8)) == 7  # E = 32674, 15 bits
+    # s = the smallest shift with 4^s >= 2 E
+    assert orc.cdc_shift(np.array([[0, 0]], dtype=np.int8)) == 0       # E = 0
+    assert orc.cdc_shift(np.array([[1, 0]], dtype=np.int8)) == 1       # 2E = 2: 4^0 < 2 <= 4^1
+    assert orc.cdc_shift(np.array([[2, 2]], dtype=np.int8)) == 2       # 2E = 16 = 4^2 (equality)
+    assert orc.cdc_shift(np.array([[3, 4]], dtype=np.int8)) == 3       # 2E = 50: 16 < 50 <= 64
+    assert orc.cdc_shift(np.array([[31, 31]] * 17, dtype=np.int8)) == 8  # 2E = 65348 <= 4^8 = 65536
     assert [orc.decim_phase(L) for L in (5, 7, 17, 19)] == [0, 1, 0, 1]
+
+
+@pytest.mark.parametrize("L", [17, 31])
+def test_cdc_shift_keeps_the_aeq_input_within_the_adc_loading(orc, L):
+    """The reading behind the shift (the paper fixes only the 5-bit width): on
+    the synthetic 75 km link, whose 5-bit samples have 5 LSB RMS, the
+    requantised AEQ input has at most that RMS and almost never saturates.
+    One shift less would load it at 6.5-8.4 LSB RMS with 2-8 % of the samples
+    at the rails, the BER floor the synthetic comparison found."""
+    import synth
+    x = synth.received(synth.rng_for(6, 3), 1 << 15, 2, 75.0, 30.0)
+    taps = synth.cd_taps(75.0, L)
+    s = orc.cdc_shift(taps)
+    xa = orc.requant_decimate(orc.cdc(x, taps), s, orc.decim_phase(L)).astype(np.float64)
+    rms_in = np.sqrt(np.mean(x.astype(np.float64) ** 2))
+    assert np.sqrt(np.mean(xa ** 2)) <= rms_in
+    assert np.mean((xa >= 15) | (xa <= -16)) < 1e-3
+    xb = orc.requant_decimate(orc.cdc(x, taps), s - 1, orc.decim_phase(L)).astype(np.float64)
+    assert np.mean((xb >= 15) | (xb <= -16)) > 1e-2
 
 
 def test_requant_decimate_hand_cases(orc):
@@ -335,11 +357,13 @@ def test_aeq_segments_continue_the_stream_with_fixed_taps(orc):
 
 
 def test_aeq_converges_on_synthetic_16qam(orc):
-    """Context, not parity: the RDE error falls on the synthetic 75 km link."""
+    """Context, not parity: the RDE error falls on the synthetic 75 km link
+    (31 CD taps, the AEQ step and centre spike of the BER comparison)."""
     import synth
-    f = synth.config2(1 << 14)
-    prm = orc.ChainParams(mu_shift=8)
-    out, _ = orc.chain(f.x, f.taps, prm)
+    n_sym = 1 << 15
+    x = synth.received(synth.rng_for(6, 2), 2 * n_sym, 2, 75.0, 22.0)
+    prm = orc.ChainParams(mu_shift=6, w0=4096)
+    out, _ = orc.chain(x, synth.cd_taps(75.0, 31), prm)
     A = prm.rde_a
     z = out.astype(np.float64)
     err = []
