@@ -92,3 +92,20 @@ def test_cfg2_stream_serial_recurrence_whole_output(orc):
     head, _ = orc.chain(f.x[: 48 * 2 * 40], f.taps, orc.ChainParams(**kw), T0=Tr)
     assert np.array_equal(got2[: head.shape[0] - 24], head[: head.shape[0] - 24])
     assert not np.array_equal(got2, got)
+
+
+def test_ber_link_chain_matches_oracle(orc):
+    """The configuration of the synthetic BER comparison: 75 km at 22 dB with
+    the library's longest CD filter (31 taps, S = 34), AEQ N = 32 adapting from
+    a centre spike of 4096 with mu_shift 6, 2^17 symbols per polarisation.
+    Every output symbol of the GPU chain equals the oracle's."""
+    n_sym = 1 << 17
+    tr = synth.transmission(synth.rng_for(6, 0), 2 * n_sym, 2, 75.0, 22.0)
+    taps = synth.cd_taps(75.0, 31)
+    plan = F.Plan(n_aeq=32, alpha_aeq=2, mu_shift=6, tap_init=4096)
+    nsym = F.chain_nsym(tr.x.shape[0], 31)
+    out = torch.full((nsym, 4), 0x5555, dtype=torch.int16, device="cuda")
+    F.cdc_aeq_run(plan, [F.Frame(torch.from_numpy(tr.x).cuda(), out, taps)])
+    torch.cuda.synchronize()
+    ref, _ = orc.chain(tr.x, taps, orc.ChainParams(n_aeq=32, alpha_aeq=2, mu_shift=6, w0=4096))
+    assert np.array_equal(out.cpu().numpy(), ref)
