@@ -348,8 +348,9 @@ FNT_API fnt_status fnt_plan_set_cdc_kernel(fnt_plan *plan, int32_t kind);
  * (FNT_FAULT_CDC_WINDOW_WAIT) of the current device's fault word, and that
  * warp stops (its blocks' outputs are not written); nothing else waits on the
  * device.  fnt_device_faults returns the fault word of the current device and,
- * with clear != 0, resets it.  Errors: FNT_ERR_INVALID (null faults),
- * FNT_ERR_CUDA. */
+ * with clear != 0, resets it.  It reads the word with a synchronous copy on
+ * the legacy default stream: synchronise the streams whose kernels it should
+ * cover first.  Errors: FNT_ERR_INVALID (null faults), FNT_ERR_CUDA. */
 #define FNT_FAULT_CDC_WINDOW_WAIT 1u
 FNT_API fnt_status fnt_device_faults(int32_t clear, uint32_t *faults);
 
