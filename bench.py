@@ -1012,7 +1012,7 @@ def main(argv=None):
     ap.add_argument("--ber-snrs", default="14,16,18,20,22,24,26", help="ber: SNRs (dB) of the sweep")
     ap.add_argument("--ber-draws", type=int, default=3, help="ber: independent draws per SNR")
     ap.add_argument("--ber-nsym", type=int, default=1 << 17, help="ber: symbols per polarisation and draw")
-    ap.add_argument("--ref-samples", type=int, default=1 << 17,
+    ap.add_argument("--ref-samples", type=int, default=1 << 16,
                     help="--impl reference, serial AEQ: stream prefix (samples) the oracle runs per step")
     args = ap.parse_args(argv)
     for wl in WORKLOADS.values():
