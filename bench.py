@@ -904,11 +904,11 @@ def _ber_float_job(job):
     and the two floating-point receivers (the comparison systems)."""
     import ber
     import synth
-    snr, seed, n_sym, skip = job
+    snr, seed, n_sym, skip, n_aeq = job
     tr = synth.transmission(synth.rng_for(6, seed), 2 * n_sym, 2, 75.0, snr)
     taps = synth.cd_taps(75.0, BER_L)
-    b_fd = ber.count_errors(ber.float_receiver(tr.analog, 75.0, mu=BER_FLOAT_MU), tr.symbols, skip).ber
-    b_tp = ber.count_errors(ber.float_receiver_taps(ber.int8_to_complex(tr.x), taps, mu=BER_FLOAT_MU),
+    b_fd = ber.count_errors(ber.float_receiver(tr.analog, 75.0, n_aeq=n_aeq, mu=BER_FLOAT_MU), tr.symbols, skip).ber
+    b_tp = ber.count_errors(ber.float_receiver_taps(ber.int8_to_complex(tr.x), taps, n_aeq=n_aeq, mu=BER_FLOAT_MU),
                             tr.symbols, skip).ber
     return dict(snr=snr, seed=seed, x=tr.x, symbols=tr.symbols, float_fd_cdc=b_fd, float_same_taps=b_tp)
 
@@ -922,7 +922,8 @@ def run_ber(args):
     import multiprocessing as mp
     snrs = [float(v) for v in args.ber_snrs.split(",")]
     n_sym, skip = args.ber_nsym, args.ber_nsym // 2
-    jobs = [(snr, seed, n_sym, skip) for snr in snrs for seed in range(args.ber_draws)]
+    na = args.ber_naeq
+    jobs = [(snr, seed, n_sym, skip, na) for snr in snrs for seed in range(args.ber_draws)]
     procs = max(1, min(len(jobs), os.cpu_count() or 1))
     t0 = time.time()
     with mp.get_context("spawn").Pool(procs) as pool:          # before any GPU work
@@ -934,7 +935,7 @@ def run_ber(args):
     import synth
     torch.cuda.set_device(0)
     taps = synth.cd_taps(75.0, BER_L)
-    plan = fnt.Plan(n_aeq=32, alpha_aeq=2, mu_shift=BER_MU_SHIFT, tap_init=BER_TAP_INIT)
+    plan = fnt.Plan(n_aeq=na, alpha_aeq=2 if na == 32 else 4080, mu_shift=BER_MU_SHIFT, tap_init=BER_TAP_INIT)
     launches = 0
     for r in results:
         x = torch.from_numpy(r["x"]).cuda()
@@ -955,7 +956,7 @@ def run_ber(args):
     at = {k: ber.snr_at_ber(snrs, curves[k]) for k in schemes}
     pen = lambda a, b: None if at[a] is None or at[b] is None else round(at[a] - at[b], 2)
     return {
-        "workload": f"ber: 75 km PDM-16QAM 40 GBaud, {n_sym} symbols per polarisation and draw, "
+        "workload": f"ber: 75 km PDM-16QAM 40 GBaud, AEQ N={na}, {n_sym} symbols per polarisation and draw, "
                     f"{args.ber_draws} draws per SNR, BER on the last {n_sym - skip} symbols, median over draws",
         "metric": "SNR at the HD-FEC BER (dB)", "hd_fec_ber": ber.HD_FEC_BER, "snr_db": snrs,
         "ber": {k: [float("%.3e" % b) for b in curves[k]] for k in schemes},
@@ -964,7 +965,7 @@ def run_ber(args):
         "penalty_db": {"fnt_vs_float_fd_cdc": pen("fnt", "float_fd_cdc"),
                        "fnt_vs_float_same_taps": pen("fnt", "float_same_taps")},
         "schemes": {"fnt": f"the GPU chain (fnt_cdc_aeq_run): FNT-CDC N=64 with {BER_L} 6-bit taps, 5-bit "
-                           f"requantisation at 1 sps, FNT-AEQ N=32 with RDE (mu_shift {BER_MU_SHIFT}, centre "
+                           f"requantisation at 1 sps, FNT-AEQ N={na} with RDE (mu_shift {BER_MU_SHIFT}, centre "
                            f"spike {BER_TAP_INIT}), from 5-bit samples",
                     "float_fd_cdc": "float64 ideal FD-CDC on the unquantised signal, float64 TD-AEQ (same RDE "
                                     f"and block schedule, mu {BER_FLOAT_MU})",
@@ -1012,6 +1013,7 @@ def main(argv=None):
     ap.add_argument("--ber-snrs", default="14,16,18,20,22,24,26", help="ber: SNRs (dB) of the sweep")
     ap.add_argument("--ber-draws", type=int, default=3, help="ber: independent draws per SNR")
     ap.add_argument("--ber-nsym", type=int, default=1 << 17, help="ber: symbols per polarisation and draw")
+    ap.add_argument("--ber-naeq", type=int, default=32, choices=(32, 64), help="ber: AEQ transform length")
     ap.add_argument("--ref-samples", type=int, default=1 << 16,
                     help="--impl reference, serial AEQ: stream prefix (samples) the oracle runs per step")
     args = ap.parse_args(argv)
