@@ -291,6 +291,7 @@ def run_fnt(args, rank, world, local_rank, oracle_pool=None):
                      aeq_warmup=warmup, aeq_update_period=wl.get("period", 1), aeq_freq_sum=wl.get("freq_sum", 0))
         p.set_tensor_gradient(args.tensor_gradient)
         p.set_aeq_kernel(args.aeq_kernel)
+        p.set_cdc_kernel(args.cdc_kernel)
         return p
 
     plan = make_plan(wl["segment"], wl["warmup"])
@@ -994,6 +995,8 @@ def main(argv=None):
                     help="AEQ segments the CPU-baseline oracle recomputes (0 = all: the whole step)")
     ap.add_argument("--ref-segments", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cdc-kernel", type=int, default=0, choices=(0, 1, 2),
+                    help="cfg2 / cfg5: CDC kernel (0 automatic, 1 a block per lane, 2 a block per 8 threads)")
     ap.add_argument("--aeq-kernel", type=int, default=0, choices=(0, 1, 2),
                     help="cfg2 / cfg5: AEQ kernel (0 automatic, 1 a warp, 2 a CTA per chain and polarisation)")
     ap.add_argument("--tensor-gradient", action="store_true",
