@@ -99,3 +99,16 @@ def test_integer_chain_converges_on_the_75km_channel(orc):
     c = ber.count_errors(ber.chain_to_complex(out), tr.symbols, skip=n_sym // 2)
     assert c.ber < 5e-3, c
     assert all(e / nb < 5e-3 for _, _, _, e, nb in c.per_pol), c.per_pol
+
+
+def test_bench_ber_host_job():
+    """bench.py's host job of the BER workload (one SNR and draw): the 5-bit
+    samples and symbols it hands to the GPU chain, and the two float
+    receivers' BERs, here on a short transmission (no GPU)."""
+    import bench
+    r = bench._ber_float_job((24.0, 5, 1 << 13, 1 << 12, 32))
+    assert r["x"].shape == (1 << 14, 2, 2) and r["x"].dtype == np.int8
+    assert r["symbols"].shape == (2, 1 << 13)
+    assert 0.0 <= r["float_fd_cdc"] <= 1.0 and 0.0 <= r["float_same_taps"] <= 1.0
+    tr = synth.transmission(synth.rng_for(6, 5), 1 << 14, 2, 75.0, 24.0)
+    assert np.array_equal(r["x"], tr.x) and np.array_equal(r["symbols"], tr.symbols)
